@@ -1,0 +1,166 @@
+"""FP64 CPU oracle for the forward and adjoint of matrix-free atomic QST.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library and its binding) never imports this package, and this package
+imports nothing from the product.
+
+The arithmetic lives in ``qst_oracle.c`` (plain C, FP64, one qubit and one
+outcome at a time); this module only compiles it with gcc, loads it with
+ctypes and marshals numpy arrays.  The definitions it follows are listed in the
+header of ``qst_oracle.c`` (Sec. II Eqs. atomic-density, born-map, qst-loss,
+atom-response, atomic-born-map; Sec. III Eqs. likelihood-ratio-vector,
+weight-gradient, atom-wirtinger-gradient, atom-projected-descent-direction,
+negative-gradient-product; Sec. IV Pauli POVM).
+
+Parity pins (tests/test_oracle_*.py): dense brute force with explicit Kronecker
+matrices, closed forms (|0...0>, GHZ, product states), linear inversion on the
+full n=4 Pauli set, POVM completeness (c == 1 gives G v = v), the identities
+<psi_k|G psi_k> = h_k and sum_k w_k h_k = sum pihat*pi/(pi+eps), and central
+finite differences of the loss.  No function here is unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "qst_oracle.c"
+_LIB = _HERE / "liboracle.so"
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile qst_oracle.c into liboracle.so with gcc (plain -O2, FP64, no fast-math)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(".so.tmp%d" % os.getpid())
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(tmp), str(_SRC), "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(str(build()))
+        P = ctypes.c_void_p
+        i32, f64 = ctypes.c_int, ctypes.c_double
+        lib.qst_oracle_forward.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, f64, P, P, P, P]
+        lib.qst_oracle_forward.restype = i32
+        lib.qst_oracle_adjoint.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P]
+        lib.qst_oracle_adjoint.restype = i32
+        lib.qst_oracle_apply_G.argtypes = [i32, i32, i32, P, P, P, P, i32, P, P]
+        lib.qst_oracle_apply_G.restype = i32
+        lib.qst_oracle_amplitude.argtypes = [i32, P, P, ctypes.c_uint32, P]
+        lib.qst_oracle_amplitude.restype = None
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _cplx(psi):
+    """complex array [..., D] -> contiguous interleaved float64 view source."""
+    return np.ascontiguousarray(np.asarray(psi, dtype=np.complex128))
+
+
+def forward(n, basis, psi, w, row_ptr, outcome, count, shots, eps=1e-8, B=None,
+            dense=False):
+    """Born probabilities, loss and likelihood ratio (FP64).
+
+    Returns dict(p_obs, c_obs, loss[, p_dense]).  ``B`` is the normalising number
+    of settings (defaults to the number passed in)."""
+    lib = _load()
+    basis = _c(basis, np.uint8)
+    M = basis.shape[0]
+    psi = _cplx(psi).reshape(-1, 1 << n)
+    K = psi.shape[0]
+    w = _c(w, np.float64)
+    row_ptr, outcome = _c(row_ptr, np.int64), _c(outcome, np.uint32)
+    count, shots = _c(count, np.uint32), _c(shots, np.uint32)
+    nnz = outcome.shape[0]
+    p_obs = np.zeros(nnz)
+    c_obs = np.zeros(nnz)
+    loss = np.zeros(1)
+    p_dense = np.zeros((M, 1 << n)) if dense else None
+    rc = lib.qst_oracle_forward(n, M, int(B or M), K, _ptr(basis), _ptr(psi), _ptr(w),
+                                _ptr(row_ptr), _ptr(outcome), _ptr(count), _ptr(shots),
+                                float(eps), _ptr(p_dense), _ptr(p_obs), _ptr(c_obs), _ptr(loss))
+    if rc != 0:
+        raise ValueError("oracle forward rejected its input")
+    out = dict(p_obs=p_obs, c_obs=c_obs, loss=float(loss[0]))
+    if dense:
+        out["p_dense"] = p_dense
+    return out
+
+
+def adjoint(n, basis, psi, w, row_ptr, outcome, c_obs, B=None):
+    """Atom gradients and coefficient gradient (FP64).
+
+    Returns dict(G_psi [K][D] complex, grad_psi = -w_k G psi_k, h [K],
+    grad_w = -h)."""
+    lib = _load()
+    basis = _c(basis, np.uint8)
+    M = basis.shape[0]
+    D = 1 << n
+    psi = _cplx(psi).reshape(-1, D)
+    K = psi.shape[0]
+    w = _c(w, np.float64)
+    row_ptr, outcome = _c(row_ptr, np.int64), _c(outcome, np.uint32)
+    c_obs = _c(c_obs, np.float64)
+    G = np.zeros((K, D), dtype=np.complex128)
+    g = np.zeros((K, D), dtype=np.complex128)
+    h = np.zeros(K)
+    rc = lib.qst_oracle_adjoint(n, M, int(B or M), K, _ptr(basis), _ptr(psi), _ptr(w),
+                                _ptr(row_ptr), _ptr(outcome), _ptr(c_obs), _ptr(G), _ptr(g), _ptr(h))
+    if rc != 0:
+        raise ValueError("oracle adjoint rejected its input")
+    return dict(G_psi=G, grad_psi=g, h=h, grad_w=-h)
+
+
+def apply_G(n, basis, row_ptr, outcome, c_obs, v, B=None):
+    """G v = (1/B) sum_s V_s^*(c_s .* V_s v) for each row of v (FP64)."""
+    lib = _load()
+    basis = _c(basis, np.uint8)
+    M = basis.shape[0]
+    D = 1 << n
+    v = _cplx(v).reshape(-1, D)
+    out = np.zeros_like(v)
+    rc = lib.qst_oracle_apply_G(n, M, int(B or M), _ptr(basis), _ptr(_c(row_ptr, np.int64)),
+                                _ptr(_c(outcome, np.uint32)), _ptr(_c(c_obs, np.float64)),
+                                v.shape[0], _ptr(v), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle apply_G rejected its input")
+    return out
+
+
+def amplitude(n, b, psi, u):
+    """(V_s psi)_u by direct summation over all basis states (independent of the
+    axis-by-axis transform)."""
+    lib = _load()
+    b = _c(b, np.uint8)
+    psi = _cplx(psi).reshape(-1)
+    out = np.zeros(2)
+    lib.qst_oracle_amplitude(n, _ptr(b), _ptr(psi), int(u), _ptr(out))
+    return complex(out[0], out[1])
+
+
+def tangent(psi, w, G_psi):
+    """Projected descent direction d_k = w_k (I - psi_k psi_k^*) G psi_k
+    (Eq. atom-projected-descent-direction), row by row, FP64."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    G_psi = np.asarray(G_psi, dtype=np.complex128)
+    inner = np.sum(np.conj(psi) * G_psi, axis=1)  # <psi_k | G psi_k>
+    return np.asarray(w, dtype=np.float64)[:, None] * (G_psi - psi * inner[:, None])
