@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: one step = forward + adjoint over one batch of synthetic data
+(n = 16 qubits, M = 4096 random Pauli settings, 2000 shots each, K = 16 atoms),
+through the C ABI of libqst.so.
+
+Prints ONE JSON line (rank 0).  Timing: W untimed warm-up steps, then K steps
+bracketed by a barrier + device synchronisation; each step is timed with CUDA
+events on the launching stream, and L2 is flushed (512 MiB write) between
+steps, outside the events.  The result is the max over ranks.  With N > 1
+ranks every rank runs an independent replica of the same workload (the
+measurement partition needs no collective on one GPU per replica).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a few settings per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint amplitudes/s (M×K×2^n), s/iteration, % roofline vs plain FP32 path"
+WORKLOAD = "n16_m4096_k16"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_ops(basis, K, D):
+    """FP32 lane operations (FADD/FMUL/FFMA each 1) of the plain butterfly method:
+    forward 2 m_s + 4 and adjoint 4 m_s + 8 per amplitude, m_s = X/Y qubits of s."""
+    m = np.count_nonzero(basis, axis=1).astype(np.float64)
+    fwd = float(np.sum(2 * m + 4)) * K * D
+    adj = float(np.sum(4 * m + 8)) * K * D
+    return fwd, adj
+
+
+def cpu_oracle_rate(inst, budget_s, settings_per_call=1, max_settings=None):
+    """Time the FP64 oracle (forward + adjoint, all K atoms) on the first settings
+    of the workload, one setting at a time, until budget_s is spent."""
+    import oracle
+    psi = inst.psi.astype(np.complex128)
+    w = inst.w.astype(np.float64)
+    done, t_total = 0, 0.0
+    while (t_total < budget_s or done < 1) and (max_settings is None or done < max_settings):
+        lo = done % inst.M
+        hi = min(lo + settings_per_call, inst.M)
+        rp = inst.row_ptr[lo:hi + 1] - inst.row_ptr[lo]
+        a, b = inst.row_ptr[lo], inst.row_ptr[hi]
+        t0 = time.perf_counter()
+        f = oracle.forward(inst.n, inst.basis[lo:hi], psi, w, rp, inst.outcome[a:b], inst.count[a:b],
+                           inst.shots[lo:hi], eps=inst.eps, B=inst.M)
+        oracle.adjoint(inst.n, inst.basis[lo:hi], psi, w, rp, inst.outcome[a:b], f["c_obs"], B=inst.M)
+        t_total += time.perf_counter() - t0
+        done += hi - lo
+    return done, t_total
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2607_19577_b300 import synth
+    inst = synth.make_instance(args.workload, seed=0)
+    per_step = 2
+    for _ in range(args.warmup):
+        cpu_oracle_rate(inst, 0.0, per_step, per_step)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(inst, 0.0, per_step, per_step)
+        t += dt
+    amps = per_step * inst.K * inst.D
+    value = amps * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": args.workload, "n": inst.n, "M": inst.M, "K": inst.K,
+                       "step": f"{per_step} settings x {inst.K} atoms x 2^{inst.n} outcomes"},
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} of {inst.M} settings per step, all {inst.K} atoms"},
+            "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2607_19577_b300 import qst, synth
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    inst = synth.make_instance(args.workload, seed=0)
+    n, M, K, D = inst.n, inst.M, inst.K, inst.D
+    plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps)
+    data = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    psi = torch.from_numpy(inst.psi).cuda()
+    w = torch.from_numpy(inst.w).cuda()
+    p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
+    c_obs = torch.empty_like(p_obs)
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(psi)
+    grad_w = torch.empty_like(w)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss)
+        plan.adjoint(psi, w, data, c_obs, grad_psi=grad, grad_w=grad_w)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+
+    plan.set_timing(True)
+    plan.reset_stats()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = plan.launch_count()
+    stats = plan.kernel_stats()
+    plan.set_timing(False)
+    plan.check()
+    ms_total = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    amps_step = M * K * D
+    value = amps_step * ws / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (the adjoint)
+    fwd_ops, adj_ops = algorithmic_ops(inst.basis, K, D)
+    la, ms_adj = stats["adjoint"]
+    lf, ms_fwd = stats["forward"]
+    adj_ms = ms_adj / max(la, 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_alu = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # TFLOP/s, 1 per lane-op
+    achieved = adj_ops / (adj_ms / 1e3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "adjoint_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": achieved / peak_alu, "traffic": traffic, "kernel": "k_adjoint",
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                               "(max SM clock of MEASURED_PEAKS.json)",
+                "ops_per_launch": adj_ops, "ms_per_launch": adj_ms,
+                "forward": {"ops_per_launch": fwd_ops, "ms_per_launch": ms_fwd / max(lf, 1),
+                            "achieved": fwd_ops / (ms_fwd / max(lf, 1) / 1e3) / 1e12}}
+    kern = {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        h_psi = torch.from_numpy(inst.psi.view(np.float32)).pin_memory().numpy().view(np.complex64)
+        h = [pin(inst.w), pin(inst.basis), pin(inst.row_ptr), pin(inst.outcome), pin(inst.count), pin(inst.shots)]
+        outs = (torch.zeros(1, dtype=torch.float64).pin_memory().numpy(),
+                torch.empty((K, 2 * D), dtype=torch.float32).pin_memory().numpy().view(np.complex64),
+                torch.empty(K, dtype=torch.float32).pin_memory().numpy())
+        for _ in range(max(1, min(args.warmup, 3))):
+            plan.evaluate_host_buffers(h_psi, *h, out=outs, stream=stream.cuda_stream)
+        if dist:
+            dist.barrier()
+        t_e2e = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.evaluate_host_buffers(h_psi, *h, out=outs, stream=stream.cuda_stream)
+            t_e2e += time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = h_psi.nbytes + sum(a.nbytes for a in h)
+        d2h = outs[0].nbytes + outs[1].nbytes + outs[2].nbytes
+        e2e = {"value": amps_step * ws / (t_e2e / args.steps), "unit": "amplitudes/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * t_e2e / args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        done, t = cpu_oracle_rate(inst, args.cpu_seconds)
+        cpu = {"value": done * K * D / t, "unit": "amplitudes/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {done} of {M} settings of the workload, all {K} atoms, forward + adjoint, "
+                         f"{t:.1f} s, single-threaded FP64 C"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "s_per_iteration": ms_step / 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded; Pauli strings uniform, Porter-Thomas surrogate counts)",
+                "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
+                           "nnz": int(inst.nnz), "precision_path": "plain FP32",
+                           "l2": "flushed between timed steps (512 MiB write outside the events)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": launches, "kernels": kern, "wall_ms_per_step": 1e3 * t_wall / args.steps,
+                "workspace_bytes": plan.workspace_bytes()}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * qst.h — C ABI of the B300 (sm_103a) forward/adjoint library for
+ * rank-adaptive matrix-free atomic quantum state tomography with local Pauli
+ * measurements.
+ *
+ * Model (Sec. II): rho = Psi diag(w) Psi^*  (Eq. atomic-density) with K atoms
+ * psi_k in C^D, D = 2^n, and weights w on the simplex.  Measurements (Sec. IV):
+ * M settings, each a Pauli string b_s in {X,Y,Z}^n, with
+ * E_{s,u} = (1/B) V_s^* |u><u| V_s, V_s = V_{b_1} (x) ... (x) V_{b_n}.
+ *
+ * Conventions shared by every entry point:
+ *   - Basis codes: 0 = Z, 1 = X, 2 = Y.  V_X = (1/sqrt2)[[1,1],[1,-1]],
+ *     V_Y = (1/sqrt2)[[1,-i],[1,i]] (outcome bit 0 <-> eigenvalue +1).
+ *   - Qubit 1 (basis[s][0]) is the most significant bit of the outcome index.
+ *   - Complex numbers are interleaved (re, im) float32 pairs ("complex64").
+ *   - Counts are CSR: row_ptr[M+1] (int64, row_ptr[0] = 0, non-decreasing,
+ *     row_ptr[M] = nnz), outcome[nnz] (uint32, < D, STRICTLY INCREASING inside
+ *     each row), count[nnz] (uint32), shots[M] (uint32, N_s, > 0 for every
+ *     non-empty row).
+ *   - pi = p / B and pihat = N_{s,u} / (B N_s), where B is
+ *     qst_params.norm_settings (0 means B = M).
+ *   - Every pointer argument of a compute call is caller-owned DEVICE memory
+ *     unless the entry point says "host".  The library never takes ownership.
+ *   - Compute calls are asynchronous on the given stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream).  Host-side argument errors return
+ *     immediately; errors found on the device (bad data, non-finite results)
+ *     are OR-ed into the plan's device status word, read with qst_plan_status.
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the
+ *     caller (they share the plan's workspace).
+ */
+#ifndef QST_H
+#define QST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qst_status {
+    QST_OK = 0,
+    QST_ERR_INVALID_ARG = 1, /* bad size, NULL where required, misaligned pointer */
+    QST_ERR_UNSUPPORTED = 2, /* size outside what this build handles (see qst_plan_create) */
+    QST_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    QST_ERR_NO_MEMORY = 4,   /* workspace allocation failed */
+    QST_ERR_DEVICE = 5       /* qst_plan_status found device-side error bits */
+} qst_status;
+
+/* Bits of the device status word. */
+#define QST_DEV_BAD_BASIS    1  /* a basis code > 2 (treated as Z) */
+#define QST_DEV_BAD_CSR      2  /* row_ptr / outcome malformed (range, order) */
+#define QST_DEV_BAD_SHOTS    4  /* shots[s] == 0 for a non-empty row */
+#define QST_DEV_NONFINITE    8  /* the loss is NaN or Inf */
+
+typedef struct qst_params {
+    double eps;           /* epsilon of Eq. qst-loss (default 1e-8) */
+    int norm_settings;    /* B; 0 = M (default 0) */
+    int chunk_qubits;     /* low qubits transformed on-chip per work unit; 0 = auto */
+    int max_bin_settings; /* cap on settings per work bin; 0 = auto */
+    int validate;         /* 1 = check basis and CSR on the device (default 1) */
+} qst_params;
+
+typedef struct qst_plan_s *qst_plan;
+
+/* Fill *p with the defaults above. */
+void qst_params_default(qst_params *p);
+
+/* Human-readable name of a status code (static string). */
+const char *qst_status_string(qst_status s);
+
+/*
+ * Create a plan for one problem shape: n qubits (1 <= n <= 16 in this build),
+ * M >= 1 settings, K >= 1 atoms, nnz >= 0 observed (setting, outcome) pairs.
+ * Allocates the device workspace (owned by the plan, freed by
+ * qst_plan_destroy) on the current CUDA device.  params may be NULL.
+ */
+qst_status qst_plan_create(qst_plan *plan, int n, int M, int K, int64_t nnz,
+                           const qst_params *params);
+qst_status qst_plan_destroy(qst_plan plan);
+
+/* Bytes of device workspace the plan holds. */
+qst_status qst_plan_workspace_bytes(qst_plan plan, int64_t *bytes);
+
+/*
+ * Forward pass (Eqs. atom-response, atomic-born-map, qst-loss,
+ * likelihood-ratio-vector):
+ *   p_{s,u} = sum_k w_k |(V_s psi_k)_u|^2,   pi = p / B,
+ *   c_{s,u} = pihat_{s,u} / (pi_{s,u} + eps) at observed outcomes,
+ *   L = - sum_{observed} pihat log(pi + eps).
+ * Inputs:  psi [K][D] complex64, w [K] float32, basis [M][n] uint8, CSR counts.
+ * Outputs (each may be NULL): p_obs [nnz] float32 (p at observed outcomes),
+ *   c_obs [nnz] float32, loss [1] float64, p_dense [M][D] float32 (every
+ *   outcome; for tests and small problems).
+ * Pointers must be 16-byte aligned for psi and 4-byte aligned otherwise.
+ */
+qst_status qst_forward(qst_plan plan, const float *psi, const float *w,
+                       const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const uint32_t *count,
+                       const uint32_t *shots, float *p_obs, float *c_obs,
+                       double *loss, float *p_dense, void *stream);
+
+/*
+ * Adjoint pass (Eqs. negative-gradient-product, atom-wirtinger-gradient,
+ * weight-gradient):
+ *   (G psi_k) = (1/B) sum_s V_s^* (c_s .* (V_s psi_k)),
+ *   grad_psi_k = dJ/dpsi_k^* = -w_k G psi_k,
+ *   grad_w_k   = dJ/dw_k     = -h_k,  h_k = (1/B) sum_{s,u} c_{s,u} |(V_s psi_k)_u|^2.
+ * c_obs [nnz] is the likelihood ratio at observed outcomes (as written by
+ * qst_forward); c is zero at every other outcome.  The rotated amplitudes are
+ * recomputed, not stored.  Outputs: grad_psi [K][D] complex64 (required),
+ * grad_w [K] float32 (may be NULL).  With w_k = -1 for every k, grad_psi is
+ * G psi_k itself (the G v product used by spectral steps).
+ */
+qst_status qst_adjoint(qst_plan plan, const float *psi, const float *w,
+                       const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const float *c_obs,
+                       float *grad_psi, float *grad_w, void *stream);
+
+/*
+ * Forward then adjoint from HOST buffers: copies the inputs to plan-owned
+ * device buffers, runs qst_forward and qst_adjoint on the stream, copies
+ * loss [1], grad_psi [K][D] complex64 and grad_w [K] back to the host buffers,
+ * and synchronises the stream.  Every pointer here is host memory (pinned
+ * memory gives asynchronous copies).  c_obs_out [nnz] may be NULL.
+ */
+qst_status qst_evaluate_host(qst_plan plan, const float *psi, const float *w,
+                             const uint8_t *basis, const int64_t *row_ptr,
+                             const uint32_t *outcome, const uint32_t *count,
+                             const uint32_t *shots, double *loss_out,
+                             float *grad_psi_out, float *grad_w_out,
+                             float *c_obs_out, void *stream);
+
+/* Synchronise the device and read (then clear) the plan's device status word.
+ * Returns QST_ERR_DEVICE if any bit was set (bits in *device_status). */
+qst_status qst_plan_status(qst_plan plan, int *device_status);
+
+/* Kernel launch accounting.  Every launch the plan issues is counted.  With
+ * timing enabled, each launch is bracketed by CUDA events on its stream;
+ * qst_plan_kernel_stats synchronises on them and returns, per kernel kind,
+ * the number of timed launches and their summed device time in ms. */
+enum {
+    QST_KERNEL_PACK = 0,
+    QST_KERNEL_VALIDATE = 1,
+    QST_KERNEL_FORWARD = 2,
+    QST_KERNEL_LOSS = 3,
+    QST_KERNEL_ADJOINT = 4,
+    QST_KERNEL_REDUCE = 5,
+    QST_KERNEL_HSUM = 6,
+    QST_KERNEL_KINDS = 7
+};
+qst_status qst_plan_set_timing(qst_plan plan, int enable);
+qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,
+                                 int kinds);
+qst_status qst_plan_reset_stats(qst_plan plan);
+/* Total kernel launches issued by this plan since creation / last reset. */
+qst_status qst_plan_launch_count(qst_plan plan, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QST_H */

@@ -1,0 +1,1138 @@
+// qst.cu — sm_103a forward/adjoint of the local-Pauli measurement oracle of
+// rank-adaptive matrix-free atomic quantum state tomography, behind the C ABI
+// declared in include/qst.h.
+//
+// Method (paper Sec. II-III, Pauli POVM of Sec. IV):
+//   forward  p_{s,u} = sum_k w_k |(V_s psi_k)_u|^2          (Eq. atomic-born-map)
+//            c = pihat / (p/B + eps),  L = -sum pihat log(p/B + eps)
+//                                                         (Eqs. qst-loss, likelihood-ratio-vector)
+//   adjoint  G psi_k = (1/B) sum_s V_s^*(c_s .* V_s psi_k) (Eq. negative-gradient-product)
+//            dJ/dpsi_k^* = -w_k G psi_k                    (Eq. atom-wirtinger-gradient)
+//            dJ/dw_k = -h_k,  h_k = a(psi_k)^T c           (Eq. weight-gradient)
+//
+// Design (one GPU, matrix-free):
+//   * V_s is a Kronecker product of 2x2 factors; Z factors are the identity and
+//     X/Y factors are add-only butterflies once the 1/sqrt2 factors are pulled
+//     out (the scale 2^-m_s, m_s = number of X/Y qubits, is applied once).
+//   * The n outcome bits are split into c low "chunk" bits, transformed on-chip
+//     (registers + shared memory), and r = n - c high bits.  Settings are binned
+//     by their basis pattern on the high bits; every setting in a bin shares the
+//     same high-bit factor U_h, so
+//         sum_{s in bin} V_s^* y_s = (U_h^* (x) I) sum_{s in bin} (I (x) U_{L,s}^*) y_s.
+//     A work unit (bin, high pattern f, atom k) therefore accumulates the inner
+//     sum for its chunk in registers across all of the bin's settings, and a
+//     reduction kernel applies U_h^* once per bin and sums the bins (compensated).
+//     The high-bit factor of the forward is applied on load, once per unit.
+//   * Inside a chunk each thread holds 2^A amplitudes (A = 5); a round applies
+//     up to A X/Y qubits in registers, and rounds are joined by transposes
+//     through XOR-swizzled shared memory.
+//   * c is zero at unobserved outcomes; it is scattered into a dense chunk
+//     buffer per setting and cleared again after use.
+//   * No atomics on the data path: every sum has a fixed order.
+#include "qst.h"
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace {
+
+constexpr int kMaxChunk = 12;   // chunk bits transformed on-chip
+constexpr int kMaxA = 5;        // register bits per round (32 amplitudes / thread)
+constexpr int kMaxRounds = 3;   // 1 + ceil((kMaxChunk - kMaxA) / kMaxA)
+constexpr int kMaxTop = 4;      // high bits handled by binning (n <= 16)
+constexpr int kMaxKeys = 81;    // 3^kMaxTop
+
+// Per-setting transform plan, written by k_pack.
+struct SetPlan {
+    uint32_t xy;               // outcome-bit mask of X/Y-measured qubits (all n bits)
+    uint32_t y;                // outcome-bit mask of Y-measured qubits
+    int32_t m;                 // popcount(xy)
+    int32_t nr;                // rounds of the chunk transform
+    uint32_t rd[kMaxRounds];   // round descriptors (see rd_* below)
+    uint32_t key;              // base-3 basis pattern of the r high bits
+};
+// round descriptor: bits [4j, 4j+4) = position of register bit j (j < 5),
+// bits [20, 25) = register bits that are X/Y, bits [25, 30) = those that are Y.
+
+struct Bin {
+    int32_t start;   // first index into the sorted setting order
+    int32_t count;   // settings in the bin
+    uint32_t xytop;  // high-bit X/Y mask, relative to bit c
+    uint32_t ytop;   // high-bit Y mask, relative to bit c
+};
+
+// ----------------------------------------------------------------- device helpers
+
+// Shared-memory XOR swizzle for complex64 arrays: the low 4 index bits are
+// XOR-ed with bits 4..7 and 8..11.  It is GF(2)-linear, so the address of
+// (base | offset) is phys(base) ^ phys(offset) for disjoint bit sets.
+__device__ __forceinline__ uint32_t phys(uint32_t u) {
+    return u ^ (((u >> 4) ^ (u >> 8)) & 15u);
+}
+
+// Scatter the low bits of src into the set bits of mask (software pdep).
+__device__ __forceinline__ uint32_t pdep(uint32_t src, uint32_t mask) {
+    uint32_t out = 0;
+    for (uint32_t bb = 1; mask; bb <<= 1) {
+        if (src & bb) out |= mask & (0u - mask);
+        mask &= mask - 1;
+    }
+    return out;
+}
+
+// Thread -> amplitude mapping of one round: thread t holds the 2^A amplitudes
+// whose register bits take every value and whose other chunk bits spell t.
+template <int A>
+struct Layout {
+    uint32_t pb;       // phys(base of this thread)
+    uint32_t P[A];     // phys(1 << position of register bit j)
+    uint32_t xyf, yf;  // which register bits are X/Y, Y
+    __device__ __forceinline__ void init(uint32_t rd, int c, uint32_t tid) {
+        uint32_t regmask = 0;
+#pragma unroll
+        for (int j = 0; j < A; ++j) {
+            const uint32_t pos = (rd >> (4 * j)) & 15u;
+            P[j] = phys(1u << pos);
+            regmask |= 1u << pos;
+        }
+        const uint32_t tmask = ((1u << c) - 1u) & ~regmask;
+        pb = phys(pdep(tid, tmask));
+        xyf = (rd >> 20) & 31u;
+        yf = (rd >> 25) & 31u;
+    }
+    __device__ __forceinline__ uint32_t at(int i) const {
+        uint32_t x = pb;
+#pragma unroll
+        for (int j = 0; j < A; ++j)
+            if ((i >> j) & 1) x ^= P[j];
+        return x;
+    }
+};
+
+// Unscaled forward factors on register bit j:  X: (a,b) -> (a+b, a-b);
+// Y: (a,b) -> (a - i b, a + i b)  (rows of [[1,-i],[1,i]]).
+template <int A>
+__device__ __forceinline__ void butterfly_fwd(float2 (&v)[1 << A], uint32_t xyf, uint32_t yf) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+        if (!((xyf >> j) & 1u)) continue;
+        if ((yf >> j) & 1u) {
+#pragma unroll
+            for (int i = 0; i < (1 << A); ++i) {
+                if ((i >> j) & 1) continue;
+                const float2 a = v[i], b = v[i | (1 << j)];
+                v[i] = make_float2(a.x + b.y, a.y - b.x);
+                v[i | (1 << j)] = make_float2(a.x - b.y, a.y + b.x);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < (1 << A); ++i) {
+                if ((i >> j) & 1) continue;
+                const float2 a = v[i], b = v[i | (1 << j)];
+                v[i] = make_float2(a.x + b.x, a.y + b.y);
+                v[i | (1 << j)] = make_float2(a.x - b.x, a.y - b.y);
+            }
+        }
+    }
+}
+
+// Conjugate-transposed factors:  X: same as forward;
+// Y: (a,b) -> (a + b, i (a - b))  (rows of [[1,1],[i,-i]]).
+template <int A>
+__device__ __forceinline__ void butterfly_inv(float2 (&v)[1 << A], uint32_t xyf, uint32_t yf) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+        if (!((xyf >> j) & 1u)) continue;
+        if ((yf >> j) & 1u) {
+#pragma unroll
+            for (int i = 0; i < (1 << A); ++i) {
+                if ((i >> j) & 1) continue;
+                const float2 a = v[i], b = v[i | (1 << j)];
+                v[i] = make_float2(a.x + b.x, a.y + b.y);
+                v[i | (1 << j)] = make_float2(b.y - a.y, a.x - b.x);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < (1 << A); ++i) {
+                if ((i >> j) & 1) continue;
+                const float2 a = v[i], b = v[i | (1 << j)];
+                v[i] = make_float2(a.x + b.x, a.y + b.y);
+                v[i | (1 << j)] = make_float2(a.x - b.x, a.y - b.y);
+            }
+        }
+    }
+}
+
+// x * i^ph
+__device__ __forceinline__ float2 mul_ipow(float2 x, int ph) {
+    switch (ph & 3) {
+        case 0: return x;
+        case 1: return make_float2(-x.y, x.x);
+        case 2: return make_float2(-x.x, -x.y);
+        default: return make_float2(x.y, -x.x);
+    }
+}
+
+// Chunk f of (U_h (x) I) psi_k, written to shared memory in the round-0 layout
+// (register bits = the top A chunk bits, thread bits = the rest).  U_h is the
+// unscaled product of the high-bit factors; Z factors select f'_j = f_j.
+template <int A>
+__device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, int c,
+                                             uint32_t f, uint32_t xytop, uint32_t ytop, uint32_t tid) {
+    constexpr int E = 1 << A;
+    float2 acc[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) acc[i] = make_float2(0.f, 0.f);
+    const int nx = __popc(xytop);
+    const int sh = c - A;
+    for (int idx = 0; idx < (1 << nx); ++idx) {
+        const uint32_t fp = (f & ~xytop) | pdep((uint32_t)idx, xytop);
+        int ph = 0;
+        for (uint32_t mm = xytop; mm; mm &= mm - 1) {
+            const int j = __ffs(mm) - 1;
+            const uint32_t fj = (f >> j) & 1u, fpj = (fp >> j) & 1u;
+            if ((ytop >> j) & 1u) {
+                if (fpj) ph += fj ? 1 : 3;
+            } else if (fj & fpj) {
+                ph += 2;
+            }
+        }
+        const float2 *base = psik + ((size_t)fp << c);
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float2 x = mul_ipow(__ldg(base + tid + ((uint32_t)i << sh)), ph);
+            acc[i].x += x.x;
+            acc[i].y += x.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < E; ++i) src[phys(tid + ((uint32_t)i << sh))] = acc[i];
+}
+
+// Forward rounds of one setting's chunk transform.  On return v holds the
+// transformed chunk in the layout of the last round, described by `lay`.
+template <int A>
+__device__ __forceinline__ void forward_rounds(float2 (&v)[1 << A], Layout<A> &lay, const SetPlan &P,
+                                               const float2 *src, float2 *work, int c, uint32_t tid) {
+    constexpr int E = 1 << A;
+    lay.init(P.rd[0], c, tid);
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = src[lay.at(i)];
+    butterfly_fwd<A>(v, lay.xyf, lay.yf);
+    for (int j = 1; j < P.nr; ++j) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) work[lay.at(i)] = v[i];
+        __syncthreads();
+        lay.init(P.rd[j], c, tid);
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = work[lay.at(i)];
+        butterfly_fwd<A>(v, lay.xyf, lay.yf);
+    }
+}
+
+// Block sum in a fixed order (deterministic), valid for any block size up to
+// kRedMax, including blocks smaller than a warp.  Result valid in thread 0.
+constexpr int kRedMax = 256;
+template <typename Tv>
+__device__ Tv block_sum(Tv x, Tv *scratch) {
+    __syncthreads();
+    scratch[threadIdx.x] = x;
+    __syncthreads();
+    Tv t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)blockDim.x; ++i) t += scratch[i];
+    return t;
+}
+
+// ----------------------------------------------------------------- kernels
+
+// Descriptor packing (Sec. IV: Pauli strings) and setting binning: one block.
+__global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis, int M, int n, int c, int r,
+                                               int smax, SetPlan *__restrict__ plans, int32_t *__restrict__ order,
+                                               Bin *__restrict__ bins, int *__restrict__ n_bins,
+                                               int *__restrict__ status) {
+    __shared__ int hist[kMaxKeys], running[kMaxKeys];
+    __shared__ int wcnt[32][kMaxKeys];
+    const int tid = threadIdx.x;
+    const int nkeys = (r == 0) ? 1 : (r == 1 ? 3 : (r == 2 ? 9 : (r == 3 ? 27 : 81)));
+    const int A = c < kMaxA ? c : kMaxA;
+    for (int i = tid; i < kMaxKeys; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int s = tid; s < M; s += blockDim.x) {
+        uint32_t xy = 0, y = 0, key = 0, p3 = 1;
+        bool bad = false;
+        for (int q = 0; q < n; ++q) {
+            int code = basis[(size_t)s * n + q];
+            if (code > 2) { bad = true; code = 0; }
+            const int pos = n - 1 - q;
+            if (code) xy |= 1u << pos;
+            if (code == 2) y |= 1u << pos;
+        }
+        for (int j = 0; j < r; ++j) {
+            const int pos = c + j;
+            const int code = ((y >> pos) & 1u) ? 2 : (((xy >> pos) & 1u) ? 1 : 0);
+            key += code * p3;
+            p3 *= 3;
+        }
+        if (bad) atomicOr(status, QST_DEV_BAD_BASIS);
+        SetPlan P;
+        P.xy = xy;
+        P.y = y;
+        P.m = __popc(xy);
+        P.key = key;
+        // round 0: the top A chunk bits
+        uint32_t rd = 0;
+        for (int j = 0; j < A; ++j) rd |= (uint32_t)(c - A + j) << (4 * j);
+        rd |= ((xy >> (c - A)) & ((1u << A) - 1u)) << 20;
+        rd |= ((y >> (c - A)) & ((1u << A) - 1u)) << 25;
+        P.rd[0] = rd;
+        int nr = 1;
+        uint32_t rem = xy & ((1u << (c - A)) - 1u);
+        while (rem && nr < kMaxRounds) {
+            uint32_t chosen = 0;
+            int cnt = 0;
+            while (rem && cnt < A) {
+                const uint32_t low = rem & (0u - rem);
+                chosen |= low;
+                rem &= rem - 1;
+                ++cnt;
+            }
+            uint32_t word = 0, xyf = 0, yf = 0;
+            int j = 0;
+            for (uint32_t cm = chosen; cm; cm &= cm - 1, ++j) {
+                const int pos = __ffs(cm) - 1;
+                word |= (uint32_t)pos << (4 * j);
+                xyf |= 1u << j;
+                if ((y >> pos) & 1u) yf |= 1u << j;
+            }
+            for (int pos = c - 1; j < A && pos >= 0; --pos) {  // identity pads
+                if ((chosen >> pos) & 1u) continue;
+                word |= (uint32_t)pos << (4 * j);
+                ++j;
+            }
+            P.rd[nr++] = word | (xyf << 20) | (yf << 25);
+        }
+        for (int j = nr; j < kMaxRounds; ++j) P.rd[j] = 0;
+        P.nr = nr;
+        plans[s] = P;
+        atomicAdd(&hist[key], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int pos = 0, nb = 0;
+        for (int key = 0; key < nkeys; ++key) {
+            running[key] = pos;
+            const int C = hist[key];
+            uint32_t xyt = 0, yt = 0;
+            int kk = key;
+            for (int j = 0; j < r; ++j, kk /= 3) {
+                const int d = kk % 3;
+                if (d) xyt |= 1u << j;
+                if (d == 2) yt |= 1u << j;
+            }
+            for (int j = 0; j < C; j += smax) {
+                Bin b;
+                b.start = pos + j;
+                b.count = (C - j) < smax ? (C - j) : smax;
+                b.xytop = xyt;
+                b.ytop = yt;
+                bins[nb++] = b;
+            }
+            pos += C;
+        }
+        *n_bins = nb;
+    }
+    __syncthreads();
+    // Stable scatter of settings into key order.
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int base = 0; base < M; base += blockDim.x) {
+        const int s = base + tid;
+        const uint32_t key = (s < M) ? plans[s].key : 0xffffffffu;
+        for (int i = lane; i < nkeys; i += 32) wcnt[wid][i] = 0;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (s < M && lane == __ffs(peers) - 1) wcnt[wid][key] = __popc(peers);
+        __syncthreads();
+        for (int key2 = tid; key2 < nkeys; key2 += blockDim.x) {
+            int acc = running[key2];
+            for (int w = 0; w < 32; ++w) {
+                const int t = wcnt[w][key2];
+                wcnt[w][key2] = acc;
+                acc += t;
+            }
+            running[key2] = acc;
+        }
+        __syncthreads();
+        if (s < M) order[wcnt[wid][key] + rank] = s;
+        __syncthreads();
+    }
+}
+
+// CSR validation and per-(setting, high pattern) offsets of the observed
+// outcomes (outcomes are sorted, so each high pattern is a contiguous range).
+// One warp per setting.  A malformed row is flagged and treated as empty.
+__global__ void k_validate(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ outcome,
+                           const uint32_t *__restrict__ shots, int M, int64_t nnz, int n, int c, int r,
+                           int validate, int32_t *__restrict__ choff, int *__restrict__ status) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= M) return;
+    const int s = gw;
+    const int nf = (1 << r) + 1;
+    int32_t *co = choff + (size_t)s * nf;
+    const int64_t lo = row_ptr[s], hi = row_ptr[s + 1];
+    int bad = 0;
+    if (validate) {
+        if (lo < 0 || hi < lo || hi > nnz || (s == 0 && lo != 0) || (s == M - 1 && hi != nnz)) bad = QST_DEV_BAD_CSR;
+        if (!bad && hi - lo > (1ll << n)) bad = QST_DEV_BAD_CSR;
+        if (!bad) {
+            const uint32_t D = 1u << n;
+            for (int64_t j = lo + lane; j < hi; j += 32) {
+                const uint32_t u = outcome[j];
+                if (u >= D || (j > lo && u <= outcome[j - 1])) bad = QST_DEV_BAD_CSR;
+            }
+            if (shots && hi > lo && shots[s] == 0u) bad |= QST_DEV_BAD_SHOTS;
+        }
+        bad = __reduce_or_sync(0xffffffffu, bad);
+    }
+    if (bad) {
+        if (lane == 0) atomicOr(status, bad);
+        for (int f = lane; f < nf; f += 32) co[f] = 0;
+        return;
+    }
+    for (int f = lane; f < nf; f += 32) {
+        int64_t a = lo, b = hi;  // first j with (outcome[j] >> c) >= f
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if ((int64_t)(outcome[mid] >> c) < f) a = mid + 1; else b = mid;
+        }
+        co[f] = (int32_t)(a - lo);
+    }
+}
+
+struct FwdArgs {
+    const float2 *psi;
+    const float *w;
+    const SetPlan *plans;
+    const int32_t *order;
+    const Bin *bins;
+    const int *n_bins;
+    const int64_t *row_ptr;
+    const uint32_t *outcome;
+    const uint32_t *count;
+    const uint32_t *shots;
+    const int32_t *choff;
+    float *pacc;       // p at observed outcomes (accumulated over atoms)
+    float *c_obs;      // optional
+    float *p_dense;    // optional [M][D]
+    double *loss_part; // [units]
+    int n, c, r, K;
+    float invB;
+    float eps;
+};
+
+// Forward unit = (bin, high pattern f).  Loops over the atoms and, per atom,
+// over the bin's settings; accumulates w_k 2^-m |(V_s psi_k)_u|^2 at the
+// observed outcomes of chunk f, then forms c and the loss terms.
+template <int A>
+__global__ void __launch_bounds__(128, 2) k_forward(const FwdArgs a) {
+    constexpr int E = 1 << A;
+    extern __shared__ float4 smem_raw[];
+    float2 *src = reinterpret_cast<float2 *>(smem_raw);
+    float2 *work = src + (1 << a.c);
+    __shared__ double red[kRedMax];
+    const uint32_t tid = threadIdx.x;
+    const int T = blockDim.x;
+    const int unit = blockIdx.x;
+    const int bin = unit >> a.r;
+    const uint32_t f = unit & ((1u << a.r) - 1u);
+    if (bin >= *a.n_bins) return;
+    const Bin b = a.bins[bin];
+    const int D = 1 << a.n;
+    const uint32_t cmask = (1u << a.c) - 1u;
+    const int nf = (1 << a.r) + 1;
+    for (int k = 0; k < a.K; ++k) {
+        const float wk = a.w[k];
+        build_source<A>(src, a.psi + (size_t)k * D, a.c, f, b.xytop, b.ytop, tid);
+        __syncthreads();
+        for (int si = 0; si < b.count; ++si) {
+            const int s = a.order[b.start + si];
+            const SetPlan P = a.plans[s];
+            float2 v[E];
+            Layout<A> lay;
+            forward_rounds<A>(v, lay, P, src, work, a.c, tid);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < E; ++i) work[lay.at(i)] = v[i];
+            __syncthreads();
+            const float sc = wk * exp2f(-(float)P.m);
+            const int64_t rb = a.row_ptr[s];
+            const int64_t lo = rb + a.choff[(size_t)s * nf + f], hi = rb + a.choff[(size_t)s * nf + f + 1];
+            for (int64_t i = lo + tid; i < hi; i += T) {
+                const float2 ph = work[phys(a.outcome[i] & cmask)];
+                const float val = sc * (ph.x * ph.x + ph.y * ph.y);
+                a.pacc[i] = (k == 0) ? val : a.pacc[i] + val;
+            }
+            if (a.p_dense) {
+                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << a.c);
+                for (uint32_t u = tid; u <= cmask; u += T) {
+                    const float2 ph = work[phys(u)];
+                    const float val = sc * (ph.x * ph.x + ph.y * ph.y);
+                    pd[u] = (k == 0) ? val : pd[u] + val;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue: likelihood ratio and loss terms at this unit's observed outcomes
+    double lsum = 0.0;
+    for (int si = 0; si < b.count; ++si) {
+        const int s = a.order[b.start + si];
+        const int64_t rb = a.row_ptr[s];
+        const int64_t lo = rb + a.choff[(size_t)s * nf + f], hi = rb + a.choff[(size_t)s * nf + f + 1];
+        const float ns = (float)a.shots[s];
+        for (int64_t i = lo + tid; i < hi; i += T) {
+            const float p = a.pacc[i];
+            const float pi = p * a.invB;
+            const float pihat = (float)a.count[i] * a.invB / ns;
+            if (a.c_obs) a.c_obs[i] = pihat / (pi + a.eps);
+            lsum -= (double)pihat * (double)logf(pi + a.eps);
+        }
+    }
+    const double t = block_sum<double>(lsum, red);
+    if (tid == 0) a.loss_part[unit] = t;
+}
+
+struct AdjArgs {
+    const float2 *psi;
+    const SetPlan *plans;
+    const int32_t *order;
+    const Bin *bins;
+    const int *n_bins;
+    const int64_t *row_ptr;
+    const uint32_t *outcome;
+    const float *c_obs;
+    const int32_t *choff;
+    float2 *zbuf;    // [bins][K][D]
+    float *hpart;    // [units]
+    int n, c, r, K;
+};
+
+// Adjoint unit = (bin, high pattern f, atom k).  For every setting of the bin:
+// recompute the chunk of V_s psi_k, multiply by c_s 2^-m (h partial sums on
+// the way), apply the conjugate-transposed chunk rounds in reverse, and add
+// into the register-resident accumulator z (round-0 layout).
+template <int A>
+__global__ void __launch_bounds__(128, 2) k_adjoint(const AdjArgs a) {
+    constexpr int E = 1 << A;
+    extern __shared__ float4 smem_raw[];
+    float2 *src = reinterpret_cast<float2 *>(smem_raw);
+    float2 *work = src + (1 << a.c);
+    float *cden = reinterpret_cast<float *>(work + (1 << a.c));
+    __shared__ float red[kRedMax];
+    const uint32_t tid = threadIdx.x;
+    const int T = blockDim.x;
+    const int unit = blockIdx.x;
+    const int k = unit % a.K;
+    const int rest = unit / a.K;
+    const uint32_t f = rest & ((1u << a.r) - 1u);
+    const int bin = rest >> a.r;
+    if (bin >= *a.n_bins) return;
+    const Bin b = a.bins[bin];
+    const int D = 1 << a.n;
+    const uint32_t cmask = (1u << a.c) - 1u;
+    const int nf = (1 << a.r) + 1;
+    for (uint32_t u = tid; u <= cmask; u += T) cden[phys(u)] = 0.f;
+    build_source<A>(src, a.psi + (size_t)k * D, a.c, f, b.xytop, b.ytop, tid);
+    __syncthreads();
+    float2 z[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) z[i] = make_float2(0.f, 0.f);
+    float hacc = 0.f;
+    for (int si = 0; si < b.count; ++si) {
+        const int s = a.order[b.start + si];
+        const SetPlan P = a.plans[s];
+        const int64_t rb = a.row_ptr[s];
+        const int64_t lo = rb + a.choff[(size_t)s * nf + f], hi = rb + a.choff[(size_t)s * nf + f + 1];
+        const float cs = exp2f(-(float)P.m);
+        for (int64_t i = lo + tid; i < hi; i += T) cden[phys(a.outcome[i] & cmask)] = a.c_obs[i] * cs;
+        float2 v[E];
+        Layout<A> lay;
+        forward_rounds<A>(v, lay, P, src, work, a.c, tid);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const float cc = cden[lay.at(i)];
+            hacc += cc * (v[i].x * v[i].x + v[i].y * v[i].y);
+            v[i].x *= cc;
+            v[i].y *= cc;
+        }
+        butterfly_inv<A>(v, lay.xyf, lay.yf);
+        for (int j = P.nr - 1; j >= 1; --j) {
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < E; ++i) work[lay.at(i)] = v[i];
+            __syncthreads();
+            lay.init(P.rd[j - 1], a.c, tid);
+#pragma unroll
+            for (int i = 0; i < E; ++i) v[i] = work[lay.at(i)];
+            butterfly_inv<A>(v, lay.xyf, lay.yf);
+        }
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            z[i].x += v[i].x;
+            z[i].y += v[i].y;
+        }
+        __syncthreads();
+        for (int64_t i = lo + tid; i < hi; i += T) cden[phys(a.outcome[i] & cmask)] = 0.f;
+        __syncthreads();
+    }
+    float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << a.c);
+    const int sh = a.c - A;
+#pragma unroll
+    for (int i = 0; i < E; ++i) zo[tid + ((uint32_t)i << sh)] = z[i];
+    const float t = block_sum<float>(hacc, red);
+    if (tid == 0) a.hpart[unit] = t;
+}
+
+// grad_k[f, l] = -(w_k / B) sum_bins (U_h^* z_{bin,k})[f, l]: the high-bit
+// conjugate-transposed factors per bin, Kahan-compensated sum over bins.
+template <int R>
+__global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf, const Bin *__restrict__ bins,
+                                                const int *__restrict__ n_bins, const float *__restrict__ w,
+                                                float2 *__restrict__ grad, int n, int c, int K, float invB) {
+    constexpr int F = 1 << R;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)K << c;
+    if (idx >= total) return;
+    const int k = (int)(idx >> c);
+    const uint32_t ul = (uint32_t)(idx & ((1 << c) - 1));
+    const int D = 1 << n;
+    float2 acc[F], cmp[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = cmp[f] = make_float2(0.f, 0.f);
+    const int nb = *n_bins;
+    for (int bi = 0; bi < nb; ++bi) {
+        const Bin b = bins[bi];
+        const float2 *zp = zbuf + ((size_t)bi * K + k) * D + ul;
+        float2 v[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) v[f] = zp[(size_t)f << c];
+        butterfly_inv<R>(v, b.xytop, b.ytop);
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            float yv = v[f].x - cmp[f].x, tv = acc[f].x + yv;
+            cmp[f].x = (tv - acc[f].x) - yv;
+            acc[f].x = tv;
+            yv = v[f].y - cmp[f].y;
+            tv = acc[f].y + yv;
+            cmp[f].y = (tv - acc[f].y) - yv;
+            acc[f].y = tv;
+        }
+    }
+    const float sc = -w[k] * invB;
+    float2 *gp = grad + (size_t)k * D + ul;
+#pragma unroll
+    for (int f = 0; f < F; ++f) gp[(size_t)f << c] = make_float2(sc * acc[f].x, sc * acc[f].y);
+}
+
+// grad_w_k = -(1/B) sum over (bin, f) units of the h partial sums (FP64).
+__global__ void __launch_bounds__(256) k_hsum(const float *__restrict__ hpart, const int *__restrict__ n_bins,
+                                              int r, int K, float invB, float *__restrict__ grad_w) {
+    __shared__ double red[kRedMax];
+    const int k = blockIdx.x;
+    const int units = *n_bins << r;
+    double s = 0.0;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) s += (double)hpart[(size_t)u * K + k];
+    const double t = block_sum<double>(s, red);
+    if (threadIdx.x == 0) grad_w[k] = (float)(-t * (double)invB);
+}
+
+// loss = sum of the forward units' partial sums (FP64, fixed order).
+__global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_part, const int *__restrict__ n_bins,
+                                              int r, double *__restrict__ loss, int *__restrict__ status) {
+    __shared__ double red[kRedMax];
+    const int units = *n_bins << r;
+    double s = 0.0;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) s += loss_part[u];
+    const double t = block_sum<double>(s, red);
+    if (threadIdx.x == 0) {
+        if (loss) *loss = t;
+        if (!isfinite(t)) atomicOr(status, QST_DEV_NONFINITE);
+    }
+}
+
+// ----------------------------------------------------------------- host side
+
+int ipow3(int r) {
+    int v = 1;
+    for (int i = 0; i < r; ++i) v *= 3;
+    return v;
+}
+
+}  // namespace
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+struct qst_plan_s {
+    int n = 0, M = 0, K = 0, c = 0, r = 0, A = 0, T = 0, smax = 0, nb_max = 0, B = 0;
+    int64_t nnz = 0;
+    qst_params prm{};
+    int device = 0;
+    // workspace
+    SetPlan *plans = nullptr;
+    int32_t *order = nullptr;
+    Bin *bins = nullptr;
+    int *n_bins = nullptr;
+    int32_t *choff = nullptr;
+    float *pacc = nullptr;
+    double *loss_part = nullptr;
+    float2 *zbuf = nullptr;
+    float *hpart = nullptr;
+    int *status = nullptr;
+    float *c_internal = nullptr;
+    int64_t ws_bytes = 0;
+    // host-buffer path (allocated on first use)
+    void *h_dev = nullptr;
+    // accounting
+    bool timing = false;
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[QST_KERNEL_KINDS] = {0};
+    double ms[QST_KERNEL_KINDS] = {0};
+    int64_t total_launches = 0;
+};
+
+namespace {
+
+template <typename Tp>
+qst_status dalloc(qst_plan p, Tp **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc((void **)ptr, count * sizeof(Tp)) != cudaSuccess) {
+        cudaGetLastError();
+        return QST_ERR_NO_MEMORY;
+    }
+    p->ws_bytes += (int64_t)(count * sizeof(Tp));
+    return QST_OK;
+}
+
+cudaEvent_t take_event(qst_plan p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <typename Fn>
+qst_status launch(qst_plan p, int kind, cudaStream_t st, Fn &&fn) {
+    TimedLaunch tl{kind, nullptr, nullptr};
+    if (p->timing) {
+        tl.start = take_event(p);
+        tl.stop = take_event(p);
+        cudaEventRecord(tl.start, st);
+    }
+    fn();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "qst: kernel launch failed: %s\n", cudaGetErrorString(e));
+        return QST_ERR_CUDA;
+    }
+    if (p->timing) {
+        cudaEventRecord(tl.stop, st);
+        p->pending.push_back(tl);
+    }
+    p->total_launches++;
+    return QST_OK;
+}
+
+void resolve_pending(qst_plan p) {
+    for (auto &tl : p->pending) {
+        cudaEventSynchronize(tl.stop);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, tl.start, tl.stop);
+        p->launches[tl.kind]++;
+        p->ms[tl.kind] += t;
+        p->pool.push_back(tl.start);
+        p->pool.push_back(tl.stop);
+    }
+    p->pending.clear();
+}
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+template <int A>
+void set_smem_attrs(int bytes_fwd, int bytes_adj) {
+    cudaFuncSetAttribute(k_forward<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_fwd);
+    cudaFuncSetAttribute(k_adjoint<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_adj);
+}
+
+qst_status prepare(qst_plan p, const uint8_t *basis, const int64_t *row_ptr, const uint32_t *outcome,
+                   const uint32_t *shots, cudaStream_t st) {
+    qst_status rc = launch(p, QST_KERNEL_PACK, st, [&] {
+        k_pack<<<1, 1024, 0, st>>>(basis, p->M, p->n, p->c, p->r, p->smax, p->plans, p->order, p->bins,
+                                   p->n_bins, p->status);
+    });
+    if (rc) return rc;
+    const int warps_per_block = 8;
+    const int grid = (p->M + warps_per_block - 1) / warps_per_block;
+    return launch(p, QST_KERNEL_VALIDATE, st, [&] {
+        k_validate<<<grid, 32 * warps_per_block, 0, st>>>(row_ptr, outcome, shots, p->M, p->nnz, p->n, p->c,
+                                                          p->r, p->prm.validate, p->choff, p->status);
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+void qst_params_default(qst_params *p) {
+    if (!p) return;
+    p->eps = 1e-8;
+    p->norm_settings = 0;
+    p->chunk_qubits = 0;
+    p->max_bin_settings = 0;
+    p->validate = 1;
+}
+
+const char *qst_status_string(qst_status s) {
+    switch (s) {
+        case QST_OK: return "ok";
+        case QST_ERR_INVALID_ARG: return "invalid argument";
+        case QST_ERR_UNSUPPORTED: return "unsupported size";
+        case QST_ERR_CUDA: return "CUDA error";
+        case QST_ERR_NO_MEMORY: return "out of device memory";
+        case QST_ERR_DEVICE: return "device-side error";
+    }
+    return "unknown status";
+}
+
+qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, const qst_params *params) {
+    if (!out) return QST_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || M < 1 || K < 1 || nnz < 0) return QST_ERR_INVALID_ARG;
+    if (nnz > (int64_t)M << n) return QST_ERR_INVALID_ARG;
+    qst_params prm;
+    qst_params_default(&prm);
+    if (params) prm = *params;
+    if (!(prm.eps >= 0.0) || prm.norm_settings < 0 || prm.max_bin_settings < 0) return QST_ERR_INVALID_ARG;
+    int c = prm.chunk_qubits ? prm.chunk_qubits : (n < kMaxChunk ? n : kMaxChunk);
+    if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
+    const int r = n - c;
+    if (r > kMaxTop) return QST_ERR_UNSUPPORTED;
+    if (K > 4096 || M > (1 << 24) || nnz > ((int64_t)1 << 31) - 1) return QST_ERR_UNSUPPORTED;
+    qst_plan p = new (std::nothrow) qst_plan_s;
+    if (!p) return QST_ERR_NO_MEMORY;
+    p->n = n;
+    p->M = M;
+    p->K = K;
+    p->nnz = nnz;
+    p->prm = prm;
+    p->c = c;
+    p->r = r;
+    p->A = c < kMaxA ? c : kMaxA;
+    p->T = 1 << (c - p->A);
+    p->B = prm.norm_settings ? prm.norm_settings : M;
+    cudaGetDevice(&p->device);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (prm.max_bin_settings) {
+        p->smax = prm.max_bin_settings;
+    } else {
+        const int64_t target = (int64_t)sms * 16;
+        int64_t s = ((int64_t)M * ((int64_t)1 << r) * K + target - 1) / target;
+        p->smax = (int)(s < 4 ? 4 : s);
+    }
+    const int nkeys = ipow3(r);
+    p->nb_max = (nkeys < M ? nkeys : M) + (M + p->smax - 1) / p->smax;
+    const int64_t D = (int64_t)1 << n;
+    const int64_t units_f = (int64_t)p->nb_max << r;
+    const int64_t units_a = units_f * K;
+    qst_status rc = QST_OK;
+    if (!rc) rc = dalloc(p, &p->plans, M);
+    if (!rc) rc = dalloc(p, &p->order, M);
+    if (!rc) rc = dalloc(p, &p->bins, p->nb_max);
+    if (!rc) rc = dalloc(p, &p->n_bins, 1);
+    if (!rc) rc = dalloc(p, &p->choff, (size_t)M * ((1 << r) + 1));
+    if (!rc) rc = dalloc(p, &p->pacc, nnz);
+    if (!rc) rc = dalloc(p, &p->c_internal, nnz);
+    if (!rc) rc = dalloc(p, &p->loss_part, units_f);
+    if (!rc) rc = dalloc(p, &p->zbuf, (size_t)p->nb_max * K * D);
+    if (!rc) rc = dalloc(p, &p->hpart, units_a);
+    if (!rc) rc = dalloc(p, &p->status, 1);
+    if (!rc && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = QST_ERR_CUDA;
+    if (!rc) {
+        // Sized for the largest chunk, so plans with different chunk sizes
+        // never lower each other's limit.
+        const int sf = 2 * (1 << kMaxChunk) * (int)sizeof(float2);
+        const int sa = sf + (1 << kMaxChunk) * (int)sizeof(float);
+        switch (p->A) {
+            case 1: set_smem_attrs<1>(sf, sa); break;
+            case 2: set_smem_attrs<2>(sf, sa); break;
+            case 3: set_smem_attrs<3>(sf, sa); break;
+            case 4: set_smem_attrs<4>(sf, sa); break;
+            default: set_smem_attrs<5>(sf, sa); break;
+        }
+        if (cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
+    }
+    if (rc) {
+        qst_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return QST_OK;
+}
+
+qst_status qst_plan_destroy(qst_plan p) {
+    if (!p) return QST_ERR_INVALID_ARG;
+    cudaFree(p->plans);
+    cudaFree(p->order);
+    cudaFree(p->bins);
+    cudaFree(p->n_bins);
+    cudaFree(p->choff);
+    cudaFree(p->pacc);
+    cudaFree(p->c_internal);
+    cudaFree(p->loss_part);
+    cudaFree(p->zbuf);
+    cudaFree(p->hpart);
+    cudaFree(p->status);
+    cudaFree(p->h_dev);
+    for (auto &tl : p->pending) {
+        cudaEventDestroy(tl.start);
+        cudaEventDestroy(tl.stop);
+    }
+    for (auto e : p->pool) cudaEventDestroy(e);
+    delete p;
+    return QST_OK;
+}
+
+qst_status qst_plan_workspace_bytes(qst_plan p, int64_t *bytes) {
+    if (!p || !bytes) return QST_ERR_INVALID_ARG;
+    *bytes = p->ws_bytes;
+    return QST_OK;
+}
+
+qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const uint32_t *count, const uint32_t *shots, float *p_obs,
+                       float *c_obs, double *loss, float *p_dense, void *stream) {
+    if (!p || !psi || !w || !basis || !row_ptr || !shots) return QST_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!outcome || !count)) return QST_ERR_INVALID_ARG;
+    if (!aligned(psi, 16) || !aligned(w, 4) || !aligned(row_ptr, 8) || (outcome && !aligned(outcome, 4)) ||
+        (count && !aligned(count, 4)) || !aligned(shots, 4) || (p_obs && !aligned(p_obs, 4)) ||
+        (c_obs && !aligned(c_obs, 4)) || (loss && !aligned(loss, 8)) || (p_dense && !aligned(p_dense, 4)))
+        return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    qst_status rc = prepare(p, basis, row_ptr, outcome, shots, st);
+    if (rc) return rc;
+    FwdArgs a;
+    a.psi = reinterpret_cast<const float2 *>(psi);
+    a.w = w;
+    a.plans = p->plans;
+    a.order = p->order;
+    a.bins = p->bins;
+    a.n_bins = p->n_bins;
+    a.row_ptr = row_ptr;
+    a.outcome = outcome;
+    a.count = count;
+    a.shots = shots;
+    a.choff = p->choff;
+    a.pacc = p_obs ? p_obs : p->pacc;
+    a.c_obs = c_obs;
+    a.p_dense = p_dense;
+    a.loss_part = p->loss_part;
+    a.n = p->n;
+    a.c = p->c;
+    a.r = p->r;
+    a.K = p->K;
+    a.invB = 1.0f / (float)p->B;
+    a.eps = (float)p->prm.eps;
+    const int grid = p->nb_max << p->r;
+    const int smem = 2 * (1 << p->c) * (int)sizeof(float2);
+    rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
+        switch (p->A) {
+            case 1: k_forward<1><<<grid, p->T, smem, st>>>(a); break;
+            case 2: k_forward<2><<<grid, p->T, smem, st>>>(a); break;
+            case 3: k_forward<3><<<grid, p->T, smem, st>>>(a); break;
+            case 4: k_forward<4><<<grid, p->T, smem, st>>>(a); break;
+            default: k_forward<5><<<grid, p->T, smem, st>>>(a); break;
+        }
+    });
+    if (rc) return rc;
+    return launch(p, QST_KERNEL_LOSS, st, [&] {
+        k_loss<<<1, 256, 0, st>>>(p->loss_part, p->n_bins, p->r, loss, p->status);
+    });
+}
+
+qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const float *c_obs, float *grad_psi, float *grad_w, void *stream) {
+    if (!p || !psi || !w || !basis || !row_ptr || !grad_psi) return QST_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!outcome || !c_obs)) return QST_ERR_INVALID_ARG;
+    if (!aligned(psi, 16) || !aligned(grad_psi, 16) || !aligned(w, 4) || !aligned(row_ptr, 8) ||
+        (outcome && !aligned(outcome, 4)) || (c_obs && !aligned(c_obs, 4)) || (grad_w && !aligned(grad_w, 4)))
+        return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // shots are only validated in the forward; the adjoint reads c directly
+    qst_status rc = prepare(p, basis, row_ptr, outcome, nullptr, st);
+    if (rc) return rc;
+    AdjArgs a;
+    a.psi = reinterpret_cast<const float2 *>(psi);
+    a.plans = p->plans;
+    a.order = p->order;
+    a.bins = p->bins;
+    a.n_bins = p->n_bins;
+    a.row_ptr = row_ptr;
+    a.outcome = outcome;
+    a.c_obs = c_obs;
+    a.choff = p->choff;
+    a.zbuf = p->zbuf;
+    a.hpart = p->hpart;
+    a.n = p->n;
+    a.c = p->c;
+    a.r = p->r;
+    a.K = p->K;
+    const int grid = (p->nb_max << p->r) * p->K;
+    const int smem = 2 * (1 << p->c) * (int)sizeof(float2) + (1 << p->c) * (int)sizeof(float);
+    rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
+        switch (p->A) {
+            case 1: k_adjoint<1><<<grid, p->T, smem, st>>>(a); break;
+            case 2: k_adjoint<2><<<grid, p->T, smem, st>>>(a); break;
+            case 3: k_adjoint<3><<<grid, p->T, smem, st>>>(a); break;
+            case 4: k_adjoint<4><<<grid, p->T, smem, st>>>(a); break;
+            default: k_adjoint<5><<<grid, p->T, smem, st>>>(a); break;
+        }
+    });
+    if (rc) return rc;
+    const float invB = 1.0f / (float)p->B;
+    const int64_t total = (int64_t)p->K << p->c;
+    const int rgrid = (int)((total + 255) / 256);
+    float2 *g = reinterpret_cast<float2 *>(grad_psi);
+    rc = launch(p, QST_KERNEL_REDUCE, st, [&] {
+        switch (p->r) {
+            case 0: k_reduce<0><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
+            case 1: k_reduce<1><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
+            case 2: k_reduce<2><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
+            case 3: k_reduce<3><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
+            default: k_reduce<4><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
+        }
+    });
+    if (rc || !grad_w) return rc;
+    return launch(p, QST_KERNEL_HSUM, st, [&] {
+        k_hsum<<<p->K, 256, 0, st>>>(p->hpart, p->n_bins, p->r, p->K, invB, grad_w);
+    });
+}
+
+qst_status qst_evaluate_host(qst_plan p, const float *psi, const float *w, const uint8_t *basis,
+                             const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
+                             const uint32_t *shots, double *loss_out, float *grad_psi_out, float *grad_w_out,
+                             float *c_obs_out, void *stream) {
+    if (!p || !psi || !w || !basis || !row_ptr || !shots || !loss_out || !grad_psi_out || !grad_w_out)
+        return QST_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!outcome || !count)) return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t D = (size_t)1 << p->n;
+    const size_t b_psi = (size_t)p->K * D * 8, b_w = (size_t)p->K * 4, b_basis = (size_t)p->M * p->n;
+    const size_t b_row = (size_t)(p->M + 1) * 8, b_nnz = (size_t)p->nnz * 4, b_shots = (size_t)p->M * 4;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_psi = 0, o_grad = o_psi + up(b_psi), o_w = o_grad + up(b_psi), o_gw = o_w + up(b_w),
+                 o_row = o_gw + up(b_w), o_out = o_row + up(b_row), o_cnt = o_out + up(b_nnz),
+                 o_c = o_cnt + up(b_nnz), o_shots = o_c + up(b_nnz), o_basis = o_shots + up(b_shots),
+                 o_loss = o_basis + up(b_basis), total = o_loss + 256;
+    if (!p->h_dev) {
+        if (cudaMalloc(&p->h_dev, total) != cudaSuccess) {
+            cudaGetLastError();
+            return QST_ERR_NO_MEMORY;
+        }
+        p->ws_bytes += (int64_t)total;
+    }
+    char *base = (char *)p->h_dev;
+#define QST_H2D(off, src, bytes)                                                                   \
+    if ((bytes) && cudaMemcpyAsync(base + (off), (src), (bytes), cudaMemcpyHostToDevice, st) != cudaSuccess) \
+        return QST_ERR_CUDA;
+    QST_H2D(o_psi, psi, b_psi);
+    QST_H2D(o_w, w, b_w);
+    QST_H2D(o_basis, basis, b_basis);
+    QST_H2D(o_row, row_ptr, b_row);
+    QST_H2D(o_out, outcome, b_nnz);
+    QST_H2D(o_cnt, count, b_nnz);
+    QST_H2D(o_shots, shots, b_shots);
+#undef QST_H2D
+    const float *d_psi = (const float *)(base + o_psi);
+    const float *d_w = (const float *)(base + o_w);
+    qst_status rc = qst_forward(p, d_psi, d_w, (const uint8_t *)(base + o_basis), (const int64_t *)(base + o_row),
+                                (const uint32_t *)(base + o_out), (const uint32_t *)(base + o_cnt),
+                                (const uint32_t *)(base + o_shots), nullptr, (float *)(base + o_c),
+                                (double *)(base + o_loss), nullptr, stream);
+    if (rc) return rc;
+    rc = qst_adjoint(p, d_psi, d_w, (const uint8_t *)(base + o_basis), (const int64_t *)(base + o_row),
+                     (const uint32_t *)(base + o_out), (const float *)(base + o_c), (float *)(base + o_grad),
+                     (float *)(base + o_gw), stream);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(loss_out, base + o_loss, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return QST_ERR_CUDA;
+    if (cudaMemcpyAsync(grad_psi_out, base + o_grad, b_psi, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return QST_ERR_CUDA;
+    if (cudaMemcpyAsync(grad_w_out, base + o_gw, b_w, cudaMemcpyDeviceToHost, st) != cudaSuccess) return QST_ERR_CUDA;
+    if (c_obs_out && b_nnz &&
+        cudaMemcpyAsync(c_obs_out, base + o_c, b_nnz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return QST_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return QST_ERR_CUDA;
+    return QST_OK;
+}
+
+qst_status qst_plan_status(qst_plan p, int *device_status) {
+    if (!p) return QST_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QST_ERR_CUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return QST_ERR_CUDA;
+    if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return QST_ERR_CUDA;
+    if (device_status) *device_status = st;
+    return st ? QST_ERR_DEVICE : QST_OK;
+}
+
+qst_status qst_plan_set_timing(qst_plan p, int enable) {
+    if (!p) return QST_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    return QST_OK;
+}
+
+qst_status qst_plan_kernel_stats(qst_plan p, int64_t *launches, double *ms, int kinds) {
+    if (!p || kinds < 0) return QST_ERR_INVALID_ARG;
+    resolve_pending(p);
+    for (int i = 0; i < kinds && i < QST_KERNEL_KINDS; ++i) {
+        if (launches) launches[i] = p->launches[i];
+        if (ms) ms[i] = p->ms[i];
+    }
+    return QST_OK;
+}
+
+qst_status qst_plan_reset_stats(qst_plan p) {
+    if (!p) return QST_ERR_INVALID_ARG;
+    resolve_pending(p);
+    for (int i = 0; i < QST_KERNEL_KINDS; ++i) {
+        p->launches[i] = 0;
+        p->ms[i] = 0.0;
+    }
+    p->total_launches = 0;
+    return QST_OK;
+}
+
+qst_status qst_plan_launch_count(qst_plan p, int64_t *count) {
+    if (!p || !count) return QST_ERR_INVALID_ARG;
+    *count = p->total_launches;
+    return QST_OK;
+}
+
+}  // extern "C"

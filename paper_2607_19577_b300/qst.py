@@ -1,0 +1,276 @@
+"""Thin Python binding of libqst.so (include/qst.h): argument marshalling only.
+
+Every step of the forward/adjoint runs in the library's CUDA kernels; this
+module checks dtypes/shapes, passes device pointers and the current CUDA
+stream, and raises on a non-OK status.  There is no CPU fallback: if the
+library is missing, ``load()`` raises.
+
+PyTorch supplies device memory and streams only.  ``QSTLoss`` wraps
+forward + adjoint as a ``torch.autograd.Function``: for a real loss PyTorch
+expects 2 * dL/dpsi^* as the gradient of a complex tensor, so backward returns
+2 * grad_output * (-w_k G psi_k) for the atoms and grad_output * (-h_k) for
+the weights.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+import torch
+
+LIB_PATH = Path(__file__).resolve().parent / "libqst.so"
+
+QST_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "unsupported size", 3: "CUDA error",
+                4: "out of device memory", 5: "device-side error"}
+DEV_BITS = {1: "bad basis code", 2: "malformed CSR counts", 4: "zero shots on a non-empty row",
+            8: "non-finite loss"}
+KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum"]
+
+
+class QSTError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("norm_settings", ctypes.c_int),
+                ("chunk_qubits", ctypes.c_int), ("max_bin_settings", ctypes.c_int),
+                ("validate", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load libqst.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise QSTError(f"{LIB_PATH} is missing: build it with paper_2607_19577_b300/build.py")
+        lib = ctypes.CDLL(str(LIB_PATH))
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        lib.qst_params_default.argtypes = [ctypes.POINTER(_Params)]
+        lib.qst_params_default.restype = None
+        lib.qst_status_string.argtypes = [i32]
+        lib.qst_status_string.restype = ctypes.c_char_p
+        lib.qst_plan_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, i64, ctypes.POINTER(_Params)]
+        lib.qst_plan_destroy.argtypes = [P]
+        lib.qst_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(i64)]
+        lib.qst_forward.argtypes = [P] + [P] * 11 + [P]
+        lib.qst_adjoint.argtypes = [P] + [P] * 8 + [P]
+        lib.qst_evaluate_host.argtypes = [P] + [P] * 11 + [P]
+        lib.qst_plan_status.argtypes = [P, ctypes.POINTER(i32)]
+        lib.qst_plan_set_timing.argtypes = [P, i32]
+        lib.qst_plan_kernel_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(f64), i32]
+        lib.qst_plan_reset_stats.argtypes = [P]
+        lib.qst_plan_launch_count.argtypes = [P, ctypes.POINTER(i64)]
+        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_forward",
+                     "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
+                     "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count"]:
+            getattr(lib, name).restype = i32
+        _lib = lib
+    return _lib
+
+
+def _check(rc, what):
+    if rc != QST_OK:
+        raise QSTError(f"{what}: {STATUS_NAMES.get(rc, rc)}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise QSTError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise QSTError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+@dataclass
+class Data:
+    """Measurement data resident on the device (Sec. IV): Pauli strings and CSR counts."""
+    n: int
+    basis: torch.Tensor     # uint8 [M][n]
+    row_ptr: torch.Tensor   # int64 [M+1]
+    outcome: torch.Tensor   # int32 view of uint32 [nnz]
+    count: torch.Tensor     # int32 view of uint32 [nnz]
+    shots: torch.Tensor     # int32 view of uint32 [M]
+
+    @property
+    def M(self):
+        return self.basis.shape[0]
+
+    @property
+    def nnz(self):
+        return self.outcome.shape[0]
+
+    @staticmethod
+    def from_numpy(n, basis, row_ptr, outcome, count, shots, device="cuda"):
+        def dev(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(device)
+        return Data(n=n, basis=dev(np.asarray(basis, np.uint8), np.uint8),
+                    row_ptr=dev(np.asarray(row_ptr, np.int64), np.int64),
+                    outcome=dev(np.asarray(outcome, np.uint32), np.int32),
+                    count=dev(np.asarray(count, np.uint32), np.int32),
+                    shots=dev(np.asarray(shots, np.uint32), np.int32))
+
+
+class Plan:
+    """Owns a qst_plan (device workspace for one problem shape)."""
+
+    def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
+                 max_bin_settings=0, validate=True):
+        lib = load()
+        prm = _Params()
+        lib.qst_params_default(ctypes.byref(prm))
+        prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
+        prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
+        h = ctypes.c_void_p()
+        _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
+               "qst_plan_create")
+        self._h, self.n, self.M, self.K, self.nnz = h, n, M, K, nnz
+        self.D = 1 << n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().qst_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self):
+        v = ctypes.c_int64()
+        _check(load().qst_plan_workspace_bytes(self._h, ctypes.byref(v)), "workspace_bytes")
+        return v.value
+
+    def _data(self, d: Data):
+        _need(d.basis, torch.uint8, (self.M, self.n), "basis")
+        _need(d.row_ptr, torch.int64, (self.M + 1,), "row_ptr")
+        _need(d.outcome, torch.int32, (self.nnz,), "outcome")
+        _need(d.count, torch.int32, (self.nnz,), "count")
+        _need(d.shots, torch.int32, (self.M,), "shots")
+
+    def forward(self, psi, w, d: Data, p_obs=None, c_obs=None, loss=None, p_dense=None):
+        """Runs qst_forward; returns (p_obs, c_obs, loss) (allocated when not given)."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(w, torch.float32, (self.K,), "w")
+        self._data(d)
+        dev = psi.device
+        p_obs = torch.empty(self.nnz, dtype=torch.float32, device=dev) if p_obs is None else p_obs
+        c_obs = torch.empty(self.nnz, dtype=torch.float32, device=dev) if c_obs is None else c_obs
+        loss = torch.empty(1, dtype=torch.float64, device=dev) if loss is None else loss
+        if p_dense is not None:
+            _need(p_dense, torch.float32, (self.M, self.D), "p_dense")
+        rc = load().qst_forward(self._h, _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr),
+                                _ptr(d.outcome), _ptr(d.count), _ptr(d.shots), _ptr(p_obs), _ptr(c_obs),
+                                _ptr(loss), _ptr(p_dense), _stream())
+        _check(rc, "qst_forward")
+        return p_obs, c_obs, loss
+
+    def adjoint(self, psi, w, d: Data, c_obs, grad_psi=None, grad_w=None):
+        """Runs qst_adjoint; returns (grad_psi = -w_k G psi_k, grad_w = -h)."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(w, torch.float32, (self.K,), "w")
+        _need(c_obs, torch.float32, (self.nnz,), "c_obs")
+        self._data(d)
+        grad_psi = torch.empty_like(psi) if grad_psi is None else grad_psi
+        grad_w = torch.empty_like(w) if grad_w is None else grad_w
+        rc = load().qst_adjoint(self._h, _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr),
+                                _ptr(d.outcome), _ptr(c_obs), _ptr(grad_psi), _ptr(grad_w), _stream())
+        _check(rc, "qst_adjoint")
+        return grad_psi, grad_w
+
+    def evaluate_host(self, psi, w, basis, row_ptr, outcome, count, shots, stream=None):
+        """Forward + adjoint from host numpy arrays (copies inside the call).
+        Returns (loss, grad_psi complex64 [K][D], grad_w float32 [K])."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex64)
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        arrs = [np.ascontiguousarray(basis, np.uint8), np.ascontiguousarray(row_ptr, np.int64),
+                np.ascontiguousarray(outcome, np.uint32), np.ascontiguousarray(count, np.uint32),
+                np.ascontiguousarray(shots, np.uint32)]
+        return self.evaluate_host_buffers(psi, w, *arrs, stream=stream)
+
+    def evaluate_host_buffers(self, psi, w, basis, row_ptr, outcome, count, shots, out=None, stream=None):
+        """Like evaluate_host, for arrays the caller keeps (e.g. pinned), with
+        optional preallocated outputs (loss[1] f64, grad_psi, grad_w)."""
+        if out is None:
+            out = (np.zeros(1, np.float64), np.empty((self.K, self.D), np.complex64), np.empty(self.K, np.float32))
+        loss, gp, gw = out
+
+        def hp(a):
+            return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+        st = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        rc = load().qst_evaluate_host(self._h, hp(psi), hp(w), hp(basis), hp(row_ptr), hp(outcome), hp(count),
+                                      hp(shots), hp(loss), hp(gp), hp(gw), None, st)
+        _check(rc, "qst_evaluate_host")
+        return float(loss[0]), gp, gw
+
+    def status(self):
+        """Synchronise and return the device status bits (0 = clean)."""
+        st = ctypes.c_int()
+        rc = load().qst_plan_status(self._h, ctypes.byref(st))
+        if rc not in (QST_OK, 5):
+            _check(rc, "qst_plan_status")
+        return st.value
+
+    def check(self):
+        st = self.status()
+        if st:
+            names = [v for b, v in DEV_BITS.items() if st & b]
+            raise QSTError("device-side error: " + ", ".join(names))
+
+    def set_timing(self, on=True):
+        _check(load().qst_plan_set_timing(self._h, int(bool(on))), "set_timing")
+
+    def kernel_stats(self):
+        n = len(KERNEL_KINDS)
+        la = (ctypes.c_int64 * n)()
+        ms = (ctypes.c_double * n)()
+        _check(load().qst_plan_kernel_stats(self._h, la, ms, n), "kernel_stats")
+        return {k: (la[i], ms[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def reset_stats(self):
+        _check(load().qst_plan_reset_stats(self._h), "reset_stats")
+
+    def launch_count(self):
+        v = ctypes.c_int64()
+        _check(load().qst_plan_launch_count(self._h, ctypes.byref(v)), "launch_count")
+        return v.value
+
+
+class QSTLoss(torch.autograd.Function):
+    """L_eps(psi, w) with the hand-written adjoint as its backward.
+
+    forward(psi complex64 [K][D], w float32 [K], plan, data) -> loss (float64 scalar).
+    The rotated amplitudes are recomputed in backward, not saved."""
+
+    @staticmethod
+    def forward(ctx, psi, w, plan: Plan, data: Data):
+        psi_c, w_c = psi.detach().contiguous(), w.detach().contiguous()
+        _, c_obs, loss = plan.forward(psi_c, w_c, data)
+        ctx.save_for_backward(psi_c, w_c, c_obs)
+        ctx.plan, ctx.data = plan, data
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        psi, w, c_obs = ctx.saved_tensors
+        grad_psi, grad_w = ctx.plan.adjoint(psi, w, ctx.data, c_obs)
+        g32 = g.to(torch.float32)
+        return 2.0 * g32 * grad_psi, g32 * grad_w, None, None
+
+
+def qst_loss(psi, w, plan: Plan, data: Data):
+    return QSTLoss.apply(psi, w, plan, data)

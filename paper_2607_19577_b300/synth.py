@@ -78,22 +78,27 @@ def counts_from_probs(probs: np.ndarray, shots: np.ndarray, rng: np.random.Gener
 def surrogate_counts(n: int, shots: np.ndarray, weights: np.ndarray, rng: np.random.Generator):
     """Counts with the statistics of Haar-like states, drawn without the Born rule.
 
-    For D <= 2^16 each setting gets outcome weights sum_r weights_r e_{r,u},
-    e ~ Exp(1) (a rank-R Porter-Thomas mixture), and a multinomial draw.  For
+    For D <= 2^16 each setting gets Porter-Thomas outcome weights (a rank-R
+    mixture sum_r weights_r e_{r,u}, e ~ Exp(1), when R*D <= 2^18, else a single
+    exponential per outcome) and N_s categorical draws by inverse CDF.  For
     larger D the N_s shots land uniformly (collisions are rare there, so the
     sparsity pattern is the same).  Returns CSR like ``counts_from_probs``."""
     D = 1 << n
     M = shots.shape[0]
+    R = weights.shape[0]
     rows, outs, cnts = [0], [], []
     for s in range(M):
+        ns = int(shots[s])
         if D <= (1 << 16):
-            e = rng.exponential(1.0, size=(weights.shape[0], D))
-            p = weights @ e
-            c = rng.multinomial(int(shots[s]), p / p.sum())
-            nz = np.nonzero(c)[0]
-            o, k = nz, c[nz]
+            if R * D <= (1 << 18):
+                p = weights @ rng.exponential(1.0, size=(R, D))
+            else:
+                p = rng.exponential(1.0, size=D)
+            cdf = np.cumsum(p)
+            draws = np.searchsorted(cdf, rng.random(ns) * cdf[-1], side="right")
+            o, k = np.unique(np.minimum(draws, D - 1), return_counts=True)
         else:
-            o, k = np.unique(rng.integers(0, D, size=int(shots[s])), return_counts=True)
+            o, k = np.unique(rng.integers(0, D, size=ns), return_counts=True)
         outs.append(o.astype(np.uint32))
         cnts.append(k.astype(np.uint32))
         rows.append(rows[-1] + o.size)
@@ -173,6 +178,13 @@ def make_instance(name: str, seed: int = 0, probs_fn=None, n=None, M=None, shots
     ``probs_fn(basis, truth_w, truth_atoms) -> [M][D]`` supplies Born
     probabilities of the truth for the counts; without it the Porter-Thomas
     surrogate is used."""
+    if name not in WORKLOADS and n is None:
+        import re
+        mt = re.fullmatch(r"n(\d+)_m(\d+)_k(\d+)(?:_s(\d+))?", name)
+        if not mt:
+            raise ValueError(f"unknown workload {name!r}")
+        n, M, K = int(mt.group(1)), int(mt.group(2)), int(mt.group(3))
+        shots = int(mt.group(4) or 2000)
     dn, dM, dshots, dK = WORKLOADS.get(name, (n, M, shots, K))
     n, M, shots, K = n or dn, M or dM, shots or dshots, K or dK
     rng = rng_for(seed, 0)
