@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--reg-bits", type=int, default=0, help="amplitudes per thread per round = 2^reg_bits (0 = auto)")
+    ap.add_argument("--chunk-qubits", type=int, default=0)
+    ap.add_argument("--max-bin-settings", type=int, default=0)
     return ap.parse_args()
 
 
@@ -181,7 +184,8 @@ def run_ours(args):
 
     inst = synth.make_instance(args.workload, seed=0)
     n, M, K, D = inst.n, inst.M, inst.K, inst.D
-    plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps)
+    plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
+                    max_bin_settings=args.max_bin_settings)
     data = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
     psi = torch.from_numpy(inst.psi).cuda()
     w = torch.from_numpy(inst.w).cuda()
@@ -308,6 +312,8 @@ def run_ours(args):
                 "data": "synthetic (seeded; Pauli strings uniform, Porter-Thomas surrogate counts)",
                 "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
                            "nnz": int(inst.nnz), "precision_path": "plain FP32",
+                           "plan": {"reg_bits": args.reg_bits, "chunk_qubits": args.chunk_qubits,
+                                    "max_bin_settings": args.max_bin_settings},
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),

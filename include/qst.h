@@ -58,6 +58,7 @@ typedef struct qst_params {
     int chunk_qubits;     /* low qubits transformed on-chip per work unit; 0 = auto */
     int max_bin_settings; /* cap on settings per work bin; 0 = auto */
     int validate;         /* 1 = check basis and CSR on the device (default 1) */
+    int reg_bits;         /* amplitudes per thread per round = 2^reg_bits: 4 or 5; 0 = auto */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;

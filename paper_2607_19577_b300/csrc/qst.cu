@@ -37,6 +37,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -46,6 +47,9 @@ constexpr int kMaxA = 5;        // register bits per round (32 amplitudes / thre
 constexpr int kMaxRounds = 3;   // 1 + ceil((kMaxChunk - kMaxA) / kMaxA)
 constexpr int kMaxTop = 4;      // high bits handled by binning (n <= 16)
 constexpr int kMaxKeys = 81;    // 3^kMaxTop
+constexpr int kMaxBin = 128;    // settings per bin (metadata staged in shared memory)
+constexpr int kStage = 1024;    // observed entries per setting staged by cp.async
+constexpr int kPaccCap = 7168;  // forward: observed entries per unit kept in shared memory
 
 // Per-setting transform plan, written by k_pack.
 struct SetPlan {
@@ -53,66 +57,49 @@ struct SetPlan {
     uint32_t y;                // outcome-bit mask of Y-measured qubits
     int32_t m;                 // popcount(xy)
     int32_t nr;                // rounds of the chunk transform
-    uint32_t rd[kMaxRounds];   // round descriptors (see rd_* below)
+    uint32_t rdA[kMaxRounds];  // register bits of each round (see below)
+    uint32_t rdB[kMaxRounds];  // thread bits of each round (see below)
     uint32_t key;              // base-3 basis pattern of the r high bits
+    uint32_t pad;
 };
-// round descriptor: bits [4j, 4j+4) = position of register bit j (j < 5),
-// bits [20, 25) = register bits that are X/Y, bits [25, 30) = those that are Y.
+// rdA: bits [4j, 4j+4) = chunk position of register bit j (j < 5), bits
+// [20, 25) = register bits that are X/Y, bits [25, 30) = those that are Y.
+// rdB: bits [4b, 4b+4) = chunk position of thread-index bit b (b < 7).  The
+// four lowest thread bits are chosen with distinct positions mod 4, so the 16
+// threads of a half-warp hit 16 distinct bank pairs under the swizzle below.
 
 struct Bin {
     int32_t start;   // first index into the sorted setting order
-    int32_t count;   // settings in the bin
+    int32_t count;   // settings in the bin (<= kMaxBin)
     uint32_t xytop;  // high-bit X/Y mask, relative to bit c
     uint32_t ytop;   // high-bit Y mask, relative to bit c
+};
+
+// A bin setting's view of chunk f, staged in shared memory per work unit.
+struct SetMeta {
+    int32_t lo;      // first CSR index of the setting's outcomes in chunk f
+    int32_t cnt;     // number of them
+    int32_t off;     // prefix of cnt over the bin (forward p accumulator)
+    float cs;        // 2^-m
 };
 
 // ----------------------------------------------------------------- device helpers
 
 // Shared-memory XOR swizzle for complex64 arrays: the low 4 index bits are
 // XOR-ed with bits 4..7 and 8..11.  It is GF(2)-linear, so the address of
-// (base | offset) is phys(base) ^ phys(offset) for disjoint bit sets.
+// (base | offset) is phys(base) ^ phys(offset) for disjoint bit sets, and
+// index bit b moves the bank pair by 2^(b mod 4).
 __device__ __forceinline__ uint32_t phys(uint32_t u) {
     return u ^ (((u >> 4) ^ (u >> 8)) & 15u);
 }
 
-// Scatter the low bits of src into the set bits of mask (software pdep).
-__device__ __forceinline__ uint32_t pdep(uint32_t src, uint32_t mask) {
-    uint32_t out = 0;
-    for (uint32_t bb = 1; mask; bb <<= 1) {
-        if (src & bb) out |= mask & (0u - mask);
-        mask &= mask - 1;
-    }
-    return out;
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-
-// Thread -> amplitude mapping of one round: thread t holds the 2^A amplitudes
-// whose register bits take every value and whose other chunk bits spell t.
-template <int A>
-struct Layout {
-    uint32_t pb;       // phys(base of this thread)
-    uint32_t P[A];     // phys(1 << position of register bit j)
-    uint32_t xyf, yf;  // which register bits are X/Y, Y
-    __device__ __forceinline__ void init(uint32_t rd, int c, uint32_t tid) {
-        uint32_t regmask = 0;
-#pragma unroll
-        for (int j = 0; j < A; ++j) {
-            const uint32_t pos = (rd >> (4 * j)) & 15u;
-            P[j] = phys(1u << pos);
-            regmask |= 1u << pos;
-        }
-        const uint32_t tmask = ((1u << c) - 1u) & ~regmask;
-        pb = phys(pdep(tid, tmask));
-        xyf = (rd >> 20) & 31u;
-        yf = (rd >> 25) & 31u;
-    }
-    __device__ __forceinline__ uint32_t at(int i) const {
-        uint32_t x = pb;
-#pragma unroll
-        for (int j = 0; j < A; ++j)
-            if ((i >> j) & 1) x ^= P[j];
-        return x;
-    }
-};
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Unscaled forward factors on register bit j:  X: (a,b) -> (a+b, a-b);
 // Y: (a,b) -> (a - i b, a + i b)  (rows of [[1,-i],[1,i]]).
@@ -178,62 +165,14 @@ __device__ __forceinline__ float2 mul_ipow(float2 x, int ph) {
     }
 }
 
-// Chunk f of (U_h (x) I) psi_k, written to shared memory in the round-0 layout
-// (register bits = the top A chunk bits, thread bits = the rest).  U_h is the
-// unscaled product of the high-bit factors; Z factors select f'_j = f_j.
-template <int A>
-__device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, int c,
-                                             uint32_t f, uint32_t xytop, uint32_t ytop, uint32_t tid) {
-    constexpr int E = 1 << A;
-    float2 acc[E];
-#pragma unroll
-    for (int i = 0; i < E; ++i) acc[i] = make_float2(0.f, 0.f);
-    const int nx = __popc(xytop);
-    const int sh = c - A;
-    for (int idx = 0; idx < (1 << nx); ++idx) {
-        const uint32_t fp = (f & ~xytop) | pdep((uint32_t)idx, xytop);
-        int ph = 0;
-        for (uint32_t mm = xytop; mm; mm &= mm - 1) {
-            const int j = __ffs(mm) - 1;
-            const uint32_t fj = (f >> j) & 1u, fpj = (fp >> j) & 1u;
-            if ((ytop >> j) & 1u) {
-                if (fpj) ph += fj ? 1 : 3;
-            } else if (fj & fpj) {
-                ph += 2;
-            }
-        }
-        const float2 *base = psik + ((size_t)fp << c);
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const float2 x = mul_ipow(__ldg(base + tid + ((uint32_t)i << sh)), ph);
-            acc[i].x += x.x;
-            acc[i].y += x.y;
-        }
+// Scatter the low bits of src into the set bits of mask (software pdep).
+__device__ __forceinline__ uint32_t pdep(uint32_t src, uint32_t mask) {
+    uint32_t out = 0;
+    for (uint32_t bb = 1; mask; bb <<= 1) {
+        if (src & bb) out |= mask & (0u - mask);
+        mask &= mask - 1;
     }
-#pragma unroll
-    for (int i = 0; i < E; ++i) src[phys(tid + ((uint32_t)i << sh))] = acc[i];
-}
-
-// Forward rounds of one setting's chunk transform.  On return v holds the
-// transformed chunk in the layout of the last round, described by `lay`.
-template <int A>
-__device__ __forceinline__ void forward_rounds(float2 (&v)[1 << A], Layout<A> &lay, const SetPlan &P,
-                                               const float2 *src, float2 *work, int c, uint32_t tid) {
-    constexpr int E = 1 << A;
-    lay.init(P.rd[0], c, tid);
-#pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = src[lay.at(i)];
-    butterfly_fwd<A>(v, lay.xyf, lay.yf);
-    for (int j = 1; j < P.nr; ++j) {
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < E; ++i) work[lay.at(i)] = v[i];
-        __syncthreads();
-        lay.init(P.rd[j], c, tid);
-#pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = work[lay.at(i)];
-        butterfly_fwd<A>(v, lay.xyf, lay.yf);
-    }
+    return out;
 }
 
 // Block sum in a fixed order (deterministic), valid for any block size up to
@@ -250,18 +189,52 @@ __device__ Tv block_sum(Tv x, Tv *scratch) {
     return t;
 }
 
+// Stage a bin's per-setting plans and chunk-f ranges in shared memory.
+// Returns (in thread 0's view and, after the barrier, everyone's) the bin's
+// total observed entries in chunk f.
+__device__ __forceinline__ void stage_bin(const Bin &b, uint32_t f, int nf, const int32_t *__restrict__ order,
+                                          const SetPlan *__restrict__ plans, const int64_t *__restrict__ row_ptr,
+                                          const int32_t *__restrict__ choff, SetPlan *plans_sm, SetMeta *meta_sm,
+                                          int *total_sm) {
+    for (int si = threadIdx.x; si < b.count; si += blockDim.x) {
+        const int s = order[b.start + si];
+        const SetPlan P = plans[s];
+        plans_sm[si] = P;
+        const int64_t rb = row_ptr[s];
+        const int32_t c0 = choff[(size_t)s * nf + f], c1 = choff[(size_t)s * nf + f + 1];
+        SetMeta mt;
+        mt.lo = (int32_t)(rb + c0);
+        mt.cnt = c1 - c0;
+        mt.off = 0;
+        mt.cs = exp2f(-(float)P.m);
+        meta_sm[si] = mt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int si = 0; si < b.count; ++si) {
+            meta_sm[si].off = acc;
+            acc += meta_sm[si].cnt;
+        }
+        *total_sm = acc;
+    }
+    __syncthreads();
+}
+
 // ----------------------------------------------------------------- kernels
 
 // Descriptor packing (Sec. IV: Pauli strings) and setting binning: one block.
 __global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis, int M, int n, int c, int r,
-                                               int smax, SetPlan *__restrict__ plans, int32_t *__restrict__ order,
+                                               int smax, int areg, SetPlan *__restrict__ plans,
+                                               int32_t *__restrict__ order,
                                                Bin *__restrict__ bins, int *__restrict__ n_bins,
                                                int *__restrict__ status) {
     __shared__ int hist[kMaxKeys], running[kMaxKeys];
     __shared__ int wcnt[32][kMaxKeys];
     const int tid = threadIdx.x;
     const int nkeys = (r == 0) ? 1 : (r == 1 ? 3 : (r == 2 ? 9 : (r == 3 ? 27 : 81)));
-    const int A = c < kMaxA ? c : kMaxA;
+    const int A = c < areg ? c : areg;
+    const int tb = c - A;  // thread-index bits
     for (int i = tid; i < kMaxKeys; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int s = tid; s < M; s += blockDim.x) {
@@ -286,39 +259,55 @@ __global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis
         P.y = y;
         P.m = __popc(xy);
         P.key = key;
-        // round 0: the top A chunk bits
-        uint32_t rd = 0;
-        for (int j = 0; j < A; ++j) rd |= (uint32_t)(c - A + j) << (4 * j);
-        rd |= ((xy >> (c - A)) & ((1u << A) - 1u)) << 20;
-        rd |= ((y >> (c - A)) & ((1u << A) - 1u)) << 25;
-        P.rd[0] = rd;
+        P.pad = 0;
+        // round 0: register bits = the top A chunk bits; thread bits ascending
+        uint32_t wa = 0, wb = 0;
+        for (int j = 0; j < A; ++j) wa |= (uint32_t)(c - A + j) << (4 * j);
+        wa |= ((xy >> (c - A)) & ((1u << A) - 1u)) << 20;
+        wa |= ((y >> (c - A)) & ((1u << A) - 1u)) << 25;
+        for (int b = 0; b < tb; ++b) wb |= (uint32_t)b << (4 * b);
+        P.rdA[0] = wa;
+        P.rdB[0] = wb;
         int nr = 1;
         uint32_t rem = xy & ((1u << (c - A)) - 1u);
         while (rem && nr < kMaxRounds) {
             uint32_t chosen = 0;
             int cnt = 0;
             while (rem && cnt < A) {
-                const uint32_t low = rem & (0u - rem);
-                chosen |= low;
+                chosen |= rem & (0u - rem);
                 rem &= rem - 1;
                 ++cnt;
             }
+            uint32_t regs = chosen;
+            for (int pos = c - 1; __popc(regs) < A && pos >= 0; --pos) regs |= 1u << pos;  // identity pads
             uint32_t word = 0, xyf = 0, yf = 0;
             int j = 0;
-            for (uint32_t cm = chosen; cm; cm &= cm - 1, ++j) {
+            for (uint32_t cm = regs; cm; cm &= cm - 1, ++j) {
                 const int pos = __ffs(cm) - 1;
                 word |= (uint32_t)pos << (4 * j);
-                xyf |= 1u << j;
-                if ((y >> pos) & 1u) yf |= 1u << j;
+                if ((chosen >> pos) & 1u) {
+                    xyf |= 1u << j;
+                    if ((y >> pos) & 1u) yf |= 1u << j;
+                }
             }
-            for (int pos = c - 1; j < A && pos >= 0; --pos) {  // identity pads
-                if ((chosen >> pos) & 1u) continue;
-                word |= (uint32_t)pos << (4 * j);
-                ++j;
+            // thread bits: lowest available position of each residue mod 4 first
+            uint32_t avail = ((1u << c) - 1u) & ~regs, tw = 0;
+            int b = 0;
+            for (int res = 0; res < 4 && b < tb; ++res) {
+                for (int pos = res; pos < c; pos += 4) {
+                    if ((avail >> pos) & 1u) {
+                        tw |= (uint32_t)pos << (4 * b++);
+                        avail &= ~(1u << pos);
+                        break;
+                    }
+                }
             }
-            P.rd[nr++] = word | (xyf << 20) | (yf << 25);
+            for (; avail && b < tb; avail &= avail - 1) tw |= (uint32_t)(__ffs(avail) - 1) << (4 * b++);
+            P.rdA[nr] = word | (xyf << 20) | (yf << 25);
+            P.rdB[nr] = tw;
+            ++nr;
         }
-        for (int j = nr; j < kMaxRounds; ++j) P.rd[j] = 0;
+        for (int j = nr; j < kMaxRounds; ++j) P.rdA[j] = P.rdB[j] = 0;
         P.nr = nr;
         plans[s] = P;
         atomicAdd(&hist[key], 1);
@@ -417,6 +406,164 @@ __global__ void k_validate(const int64_t *__restrict__ row_ptr, const uint32_t *
     }
 }
 
+// Compile-time geometry of a chunk of 2^C amplitudes.
+template <int C, int RA>
+struct Geo {
+    static constexpr int A = C < RA ? C : RA;        // register bits per round
+    static constexpr int E = 1 << A;                 // amplitudes per thread
+    static constexpr int TB = C - A;                 // thread-index bits
+    static constexpr int T = 1 << TB;                // threads per unit
+    static constexpr int N = 1 << C;                 // chunk size
+};
+
+__host__ __device__ constexpr int ctz_c(int t) { return (t & 1) ? 0 : 1 + ctz_c(t >> 1); }
+
+// Gray-code walk over the 2^A register elements: step t flips register bit
+// ctz(t), so each element's offset is one XOR away from the previous one.
+// Template recursion keeps every index a compile-time constant.
+template <int A, int t>
+struct GrayWalk {
+    template <typename Fn>
+    __device__ __forceinline__ static void run(uint32_t x, const uint32_t (&P8)[A], Fn &fn) {
+        constexpr int j = ctz_c(t);
+        x ^= P8[j];
+        fn(std::integral_constant<int, (t ^ (t >> 1))>(), x);
+        GrayWalk<A, t + 1>::run(x, P8, fn);
+    }
+};
+template <int A>
+struct GrayWalk<A, (1 << A)> {
+    template <typename Fn>
+    __device__ __forceinline__ static void run(uint32_t, const uint32_t (&)[A], Fn &) {}
+};
+
+// Thread -> amplitude mapping of one round, as byte offsets into a swizzled
+// complex64 buffer: thread t holds the 2^A amplitudes whose register bits take
+// every value and whose other chunk bits spell t.  Offsets are generated along
+// a Gray code, one XOR per amplitude.
+template <int C, int RA>
+struct Lay {
+    using G = Geo<C, RA>;
+    uint32_t b8;          // 8 * phys(base of this thread)
+    uint32_t P8[G::A];    // 8 * phys(1 << position of register bit j)
+    uint32_t xyf, yf;     // which register bits are X/Y, Y
+    __device__ __forceinline__ void init(uint32_t rdA, uint32_t rdB, uint32_t tid) {
+#pragma unroll
+        for (int j = 0; j < G::A; ++j) P8[j] = phys(1u << ((rdA >> (4 * j)) & 15u)) << 3;
+        uint32_t base = 0;
+#pragma unroll
+        for (int b = 0; b < G::TB; ++b) base |= ((tid >> b) & 1u) << ((rdB >> (4 * b)) & 15u);
+        b8 = phys(base) << 3;
+        xyf = (rdA >> 20) & 31u;
+        yf = (rdA >> 25) & 31u;
+    }
+    // fn(integral_constant<i>, byte offset of register element i), every i once
+    template <typename Fn>
+    __device__ __forceinline__ void walk(Fn &&fn) const {
+        fn(std::integral_constant<int, 0>(), b8);
+        GrayWalk<G::A, 1>::run(b8, P8, fn);
+    }
+};
+
+__device__ __forceinline__ float2 lds2(const unsigned char *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void sts2(unsigned char *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+
+// Chunk f of (U_h (x) I) psi_k, written to shared memory "i-major": register
+// element i of thread t (amplitude t + i 2^TB) at index i 2^TB + t.  U_h is
+// the unscaled product of the high-bit factors; Z factors select f'_j = f_j.
+template <int C, int RA>
+__device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, uint32_t f,
+                                             uint32_t xytop, uint32_t ytop, uint32_t tid) {
+    using G = Geo<C, RA>;
+    float2 acc[G::E];
+#pragma unroll
+    for (int i = 0; i < G::E; ++i) acc[i] = make_float2(0.f, 0.f);
+    const int nx = __popc(xytop);
+    // coefficient phase i^ph of source chunk f' in output chunk f
+    auto chunk = [&](int idx, int &ph) {
+        const uint32_t fp = (f & ~xytop) | pdep((uint32_t)idx, xytop);
+        ph = 0;
+        for (uint32_t mm = xytop; mm; mm &= mm - 1) {
+            const int j = __ffs(mm) - 1;
+            const uint32_t fj = (f >> j) & 1u, fpj = (fp >> j) & 1u;
+            if ((ytop >> j) & 1u) {
+                if (fpj) ph += fj ? 1 : 3;
+            } else if (fj & fpj) {
+                ph += 2;
+            }
+        }
+        return psik + ((size_t)fp << C) + tid;
+    };
+    const int nidx = 1 << nx;
+    int idx = 0;
+    for (; idx + 1 < nidx; idx += 2) {  // two chunks in flight per step
+        int ph0, ph1;
+        const float2 *b0 = chunk(idx, ph0), *b1 = chunk(idx + 1, ph1);
+        float2 x0[G::E], x1[G::E];
+#pragma unroll
+        for (int i = 0; i < G::E; ++i) {
+            x0[i] = __ldg(b0 + (i << G::TB));
+            x1[i] = __ldg(b1 + (i << G::TB));
+        }
+#pragma unroll
+        for (int i = 0; i < G::E; ++i) {
+            const float2 y0 = mul_ipow(x0[i], ph0), y1 = mul_ipow(x1[i], ph1);
+            acc[i].x += y0.x + y1.x;
+            acc[i].y += y0.y + y1.y;
+        }
+    }
+    if (idx < nidx) {
+        int ph0;
+        const float2 *b0 = chunk(idx, ph0);
+#pragma unroll
+        for (int i = 0; i < G::E; ++i) {
+            const float2 y0 = mul_ipow(__ldg(b0 + (i << G::TB)), ph0);
+            acc[i].x += y0.x;
+            acc[i].y += y0.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < G::E; ++i) src[(i << G::TB) + tid] = acc[i];
+}
+
+// Forward rounds of one setting's chunk transform.  On return v holds the
+// transformed chunk in the layout of the last round, described by L.
+template <int C, int RA>
+__device__ __forceinline__ void forward_rounds(float2 (&v)[Geo<C, RA>::E], Lay<C, RA> &L, const SetPlan &P,
+                                               const float2 *src, unsigned char *work, uint32_t tid) {
+    using G = Geo<C, RA>;
+    L.init(P.rdA[0], P.rdB[0], tid);
+#pragma unroll
+    for (int i = 0; i < G::E; ++i) v[i] = src[(i << G::TB) + tid];
+    const int nr = P.nr;
+    for (int j = 0;; ++j) {  // one butterfly site keeps the unrolled code small
+        butterfly_fwd<G::A>(v, L.xyf, L.yf);
+        if (j + 1 >= nr) break;
+        __syncthreads();
+        L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
+        __syncthreads();
+        L.init(P.rdA[j + 1], P.rdB[j + 1], tid);
+        L.walk([&](auto ic, uint32_t x) { v[decltype(ic)::value] = lds2(work + x); });
+    }
+}
+
+// Shared-memory plan of the two hot kernels (bytes, for a chunk of 2^c).
+struct SmemPlan {
+    int src, work, cden, stage, plans, meta, pacc, total;
+};
+__host__ __device__ constexpr SmemPlan smem_plan(int c, bool adjoint, int pacc_cap) {
+    SmemPlan sp{};
+    sp.src = 0;
+    sp.work = sp.src + (8 << c);
+    sp.cden = sp.work + (8 << c);
+    sp.stage = sp.cden + (adjoint ? (4 << c) : 0);
+    sp.plans = sp.stage + 2 * kStage * (adjoint ? 8 : 4);
+    sp.meta = sp.plans + kMaxBin * (int)sizeof(SetPlan);
+    sp.pacc = sp.meta + kMaxBin * (int)sizeof(SetMeta);
+    sp.total = sp.pacc + (adjoint ? 0 : 4 * pacc_cap);
+    return sp;
+}
+
 struct FwdArgs {
     const float2 *psi;
     const float *w;
@@ -429,80 +576,107 @@ struct FwdArgs {
     const uint32_t *count;
     const uint32_t *shots;
     const int32_t *choff;
-    float *pacc;       // p at observed outcomes (accumulated over atoms)
-    float *c_obs;      // optional
+    float *pacc;       // p at observed outcomes when the bin exceeds the shared accumulator
+    float *p_obs;      // optional output
+    float *c_obs;      // optional output
     float *p_dense;    // optional [M][D]
     double *loss_part; // [units]
-    int n, c, r, K;
+    int n, r, K;
     float invB;
     float eps;
 };
 
 // Forward unit = (bin, high pattern f).  Loops over the atoms and, per atom,
 // over the bin's settings; accumulates w_k 2^-m |(V_s psi_k)_u|^2 at the
-// observed outcomes of chunk f, then forms c and the loss terms.
-template <int A>
-__global__ void __launch_bounds__(128, 2) k_forward(const FwdArgs a) {
-    constexpr int E = 1 << A;
-    extern __shared__ float4 smem_raw[];
-    float2 *src = reinterpret_cast<float2 *>(smem_raw);
-    float2 *work = src + (1 << a.c);
+// observed outcomes of chunk f (in shared memory when they fit), then forms c
+// and the loss terms.  The next setting's outcome indices are prefetched with
+// cp.async while the current one is transformed.
+template <int C, int RA>
+__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
+    using G = Geo<C, RA>;
+    constexpr SmemPlan sp = smem_plan(C, false, kPaccCap);
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *src = reinterpret_cast<float2 *>(smem + sp.src);
+    unsigned char *work = smem + sp.work;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem + sp.stage);
+    SetPlan *plans_sm = reinterpret_cast<SetPlan *>(smem + sp.plans);
+    SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
+    float *pacc_sm = reinterpret_cast<float *>(smem + sp.pacc);
     __shared__ double red[kRedMax];
+    __shared__ int total_sm;
     const uint32_t tid = threadIdx.x;
-    const int T = blockDim.x;
     const int unit = blockIdx.x;
     const int bin = unit >> a.r;
     const uint32_t f = unit & ((1u << a.r) - 1u);
     if (bin >= *a.n_bins) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
-    const uint32_t cmask = (1u << a.c) - 1u;
-    const int nf = (1 << a.r) + 1;
+    constexpr uint32_t cmask = G::N - 1;
+    stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, plans_sm, meta_sm, &total_sm);
+    const bool in_sm = total_sm <= kPaccCap;
+    const int bcount = b.count;
+    const uint32_t *outcome = a.outcome;
+    auto issue = [=](int si) {
+        if (si < bcount) {
+            const SetMeta mt = meta_sm[si];
+            uint32_t *dst = stage + (si & 1) * kStage;
+            const int nst = mt.cnt < kStage ? mt.cnt : kStage;
+            for (int j = tid; j < nst; j += G::T) cp_async4(dst + j, outcome + mt.lo + j);
+        }
+        cp_async_commit();
+    };
     for (int k = 0; k < a.K; ++k) {
         const float wk = a.w[k];
-        build_source<A>(src, a.psi + (size_t)k * D, a.c, f, b.xytop, b.ytop, tid);
+        build_source<C, RA>(src, a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
+        issue(0);
         __syncthreads();
         for (int si = 0; si < b.count; ++si) {
-            const int s = a.order[b.start + si];
-            const SetPlan P = a.plans[s];
-            float2 v[E];
-            Layout<A> lay;
-            forward_rounds<A>(v, lay, P, src, work, a.c, tid);
+            issue(si + 1);
+            const SetPlan &P = plans_sm[si];
+            const SetMeta mt = meta_sm[si];
+            float2 v[G::E];
+            Lay<C, RA> L;
+            forward_rounds<C, RA>(v, L, P, src, work, tid);
+            cp_async_wait1();
             __syncthreads();
-#pragma unroll
-            for (int i = 0; i < E; ++i) work[lay.at(i)] = v[i];
+            L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
             __syncthreads();
-            const float sc = wk * exp2f(-(float)P.m);
-            const int64_t rb = a.row_ptr[s];
-            const int64_t lo = rb + a.choff[(size_t)s * nf + f], hi = rb + a.choff[(size_t)s * nf + f + 1];
-            for (int64_t i = lo + tid; i < hi; i += T) {
-                const float2 ph = work[phys(a.outcome[i] & cmask)];
+            const float sc = wk * mt.cs;
+            const uint32_t *st = stage + (si & 1) * kStage;
+            for (int j = tid; j < mt.cnt; j += G::T) {
+                const uint32_t u = (j < kStage ? st[j] : a.outcome[mt.lo + j]) & cmask;
+                const float2 ph = lds2(work + (phys(u) << 3));
                 const float val = sc * (ph.x * ph.x + ph.y * ph.y);
-                a.pacc[i] = (k == 0) ? val : a.pacc[i] + val;
+                float *pp = in_sm ? pacc_sm + mt.off + j : a.pacc + mt.lo + j;
+                *pp = (k == 0) ? val : *pp + val;
             }
             if (a.p_dense) {
-                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << a.c);
-                for (uint32_t u = tid; u <= cmask; u += T) {
-                    const float2 ph = work[phys(u)];
+                const int s = a.order[b.start + si];
+                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
+                for (uint32_t u = tid; u <= cmask; u += G::T) {
+                    const float2 ph = lds2(work + (phys(u) << 3));
                     const float val = sc * (ph.x * ph.x + ph.y * ph.y);
                     pd[u] = (k == 0) ? val : pd[u] + val;
                 }
             }
+            __syncthreads();  // stage buffer and work are reused by the next setting
         }
+        cp_async_wait0();
         __syncthreads();
     }
     // epilogue: likelihood ratio and loss terms at this unit's observed outcomes
     double lsum = 0.0;
     for (int si = 0; si < b.count; ++si) {
+        const SetMeta mt = meta_sm[si];
         const int s = a.order[b.start + si];
-        const int64_t rb = a.row_ptr[s];
-        const int64_t lo = rb + a.choff[(size_t)s * nf + f], hi = rb + a.choff[(size_t)s * nf + f + 1];
         const float ns = (float)a.shots[s];
-        for (int64_t i = lo + tid; i < hi; i += T) {
-            const float p = a.pacc[i];
+        for (int j = tid; j < mt.cnt; j += G::T) {
+            const int64_t i = (int64_t)mt.lo + j;
+            const float p = in_sm ? pacc_sm[mt.off + j] : a.pacc[i];
             const float pi = p * a.invB;
             const float pihat = (float)a.count[i] * a.invB / ns;
             if (a.c_obs) a.c_obs[i] = pihat / (pi + a.eps);
+            if (a.p_obs) a.p_obs[i] = p;
             lsum -= (double)pihat * (double)logf(pi + a.eps);
         }
     }
@@ -522,23 +696,30 @@ struct AdjArgs {
     const int32_t *choff;
     float2 *zbuf;    // [bins][K][D]
     float *hpart;    // [units]
-    int n, c, r, K;
+    int n, r, K;
 };
 
 // Adjoint unit = (bin, high pattern f, atom k).  For every setting of the bin:
 // recompute the chunk of V_s psi_k, multiply by c_s 2^-m (h partial sums on
 // the way), apply the conjugate-transposed chunk rounds in reverse, and add
-// into the register-resident accumulator z (round-0 layout).
-template <int A>
-__global__ void __launch_bounds__(128, 2) k_adjoint(const AdjArgs a) {
-    constexpr int E = 1 << A;
-    extern __shared__ float4 smem_raw[];
-    float2 *src = reinterpret_cast<float2 *>(smem_raw);
-    float2 *work = src + (1 << a.c);
-    float *cden = reinterpret_cast<float *>(work + (1 << a.c));
+// into the register-resident accumulator z (round-0 layout).  The next
+// setting's (outcome, c) pairs are prefetched with cp.async and scattered into
+// the dense c buffer at the end of the current setting.
+template <int C, int RA>
+__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
+    using G = Geo<C, RA>;
+    constexpr SmemPlan sp = smem_plan(C, true, 0);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const float2 *src = reinterpret_cast<const float2 *>(smem + sp.src);
+    unsigned char *work = smem + sp.work;
+    unsigned char *cdb = smem + sp.cden;  // float per amplitude, swizzled index
+    uint32_t *stage_u = reinterpret_cast<uint32_t *>(smem + sp.stage);
+    float *stage_c = reinterpret_cast<float *>(smem + sp.stage + 2 * kStage * 4);
+    SetPlan *plans_sm = reinterpret_cast<SetPlan *>(smem + sp.plans);
+    SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
     __shared__ float red[kRedMax];
+    __shared__ int total_sm;
     const uint32_t tid = threadIdx.x;
-    const int T = blockDim.x;
     const int unit = blockIdx.x;
     const int k = unit % a.K;
     const int rest = unit / a.K;
@@ -547,57 +728,85 @@ __global__ void __launch_bounds__(128, 2) k_adjoint(const AdjArgs a) {
     if (bin >= *a.n_bins) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
-    const uint32_t cmask = (1u << a.c) - 1u;
-    const int nf = (1 << a.r) + 1;
-    for (uint32_t u = tid; u <= cmask; u += T) cden[phys(u)] = 0.f;
-    build_source<A>(src, a.psi + (size_t)k * D, a.c, f, b.xytop, b.ytop, tid);
-    __syncthreads();
-    float2 z[E];
+    constexpr uint32_t cmask = G::N - 1;
+    float *cden = reinterpret_cast<float *>(cdb);
+    for (uint32_t u = tid; u <= cmask; u += G::T) cden[u] = 0.f;
+    stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, plans_sm, meta_sm, &total_sm);
+    const int bcount = b.count;
+    const uint32_t *outcome = a.outcome;
+    const float *c_obs = a.c_obs;
+    auto issue = [=](int si) {
+        if (si < bcount) {
+            const SetMeta mt = meta_sm[si];
+            const int nst = mt.cnt < kStage ? mt.cnt : kStage;
+            uint32_t *du = stage_u + (si & 1) * kStage;
+            float *dc = stage_c + (si & 1) * kStage;
+            for (int j = tid; j < nst; j += G::T) {
+                cp_async4(du + j, outcome + mt.lo + j);
+                cp_async4(dc + j, c_obs + mt.lo + j);
+            }
+        }
+        cp_async_commit();
+    };
+    // scatter (val = c 2^-m) or clear (val = 0) setting si's entries of the
+    // dense c buffer; each thread touches the entries it staged itself.
+    auto scatter = [=](int si, bool clear) {
+        const SetMeta mt = meta_sm[si];
+        const uint32_t *su = stage_u + (si & 1) * kStage;
+        const float *sc = stage_c + (si & 1) * kStage;
+        for (int j = tid; j < mt.cnt; j += G::T) {
+            const bool st = j < kStage;
+            const uint32_t u = (st ? su[j] : outcome[mt.lo + j]) & cmask;
+            cden[phys(u)] = clear ? 0.f : (st ? sc[j] : c_obs[mt.lo + j]) * mt.cs;
+        }
+    };
+    issue(0);
+    build_source<C, RA>(const_cast<float2 *>(src), a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
+    cp_async_wait0();
+    __syncthreads();  // c buffer zeroed, source built
+    if (b.count > 0) scatter(0, false);
+    float2 z[G::E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) z[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < G::E; ++i) z[i] = make_float2(0.f, 0.f);
     float hacc = 0.f;
     for (int si = 0; si < b.count; ++si) {
-        const int s = a.order[b.start + si];
-        const SetPlan P = a.plans[s];
-        const int64_t rb = a.row_ptr[s];
-        const int64_t lo = rb + a.choff[(size_t)s * nf + f], hi = rb + a.choff[(size_t)s * nf + f + 1];
-        const float cs = exp2f(-(float)P.m);
-        for (int64_t i = lo + tid; i < hi; i += T) cden[phys(a.outcome[i] & cmask)] = a.c_obs[i] * cs;
-        float2 v[E];
-        Layout<A> lay;
-        forward_rounds<A>(v, lay, P, src, work, a.c, tid);
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            const float cc = cden[lay.at(i)];
+        issue(si + 1);
+        const SetPlan &P = plans_sm[si];
+        const int nr = P.nr;
+        float2 v[G::E];
+        Lay<C, RA> L;
+        forward_rounds<C, RA>(v, L, P, src, work, tid);
+        if (nr == 1) __syncthreads();  // this setting's c scatter is visible
+        L.walk([&](auto ic, uint32_t x) {
+            constexpr int i = decltype(ic)::value;
+            const float cc = *reinterpret_cast<const float *>(cdb + (x >> 1));
             hacc += cc * (v[i].x * v[i].x + v[i].y * v[i].y);
             v[i].x *= cc;
             v[i].y *= cc;
-        }
-        butterfly_inv<A>(v, lay.xyf, lay.yf);
-        for (int j = P.nr - 1; j >= 1; --j) {
+        });
+        for (int j = nr - 1;; --j) {  // one butterfly site
+            butterfly_inv<G::A>(v, L.xyf, L.yf);
+            if (j == 0) break;
             __syncthreads();
-#pragma unroll
-            for (int i = 0; i < E; ++i) work[lay.at(i)] = v[i];
+            L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
             __syncthreads();
-            lay.init(P.rd[j - 1], a.c, tid);
-#pragma unroll
-            for (int i = 0; i < E; ++i) v[i] = work[lay.at(i)];
-            butterfly_inv<A>(v, lay.xyf, lay.yf);
+            L.init(P.rdA[j - 1], P.rdB[j - 1], tid);
+            L.walk([&](auto ic, uint32_t x) { v[decltype(ic)::value] = lds2(work + x); });
         }
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
+        for (int i = 0; i < G::E; ++i) {
             z[i].x += v[i].x;
             z[i].y += v[i].y;
         }
-        __syncthreads();
-        for (int64_t i = lo + tid; i < hi; i += T) cden[phys(a.outcome[i] & cmask)] = 0.f;
-        __syncthreads();
+        if (nr == 1) __syncthreads();  // every thread is done reading the c buffer
+        scatter(si, true);
+        cp_async_wait0();
+        __syncthreads();  // cleared before the next scatter; stage free for reuse
+        if (si + 1 < b.count) scatter(si + 1, false);
     }
-    float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << a.c);
-    const int sh = a.c - A;
+    float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << C);
 #pragma unroll
-    for (int i = 0; i < E; ++i) zo[tid + ((uint32_t)i << sh)] = z[i];
+    for (int i = 0; i < G::E; ++i) zo[tid + (i << G::TB)] = z[i];
     const float t = block_sum<float>(hacc, red);
     if (tid == 0) a.hpart[unit] = t;
 }
@@ -775,17 +984,45 @@ void resolve_pending(qst_plan p) {
 
 bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
-template <int A>
-void set_smem_attrs(int bytes_fwd, int bytes_adj) {
-    cudaFuncSetAttribute(k_forward<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_fwd);
-    cudaFuncSetAttribute(k_adjoint<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_adj);
+template <int C, int RA>
+void set_smem_attrs() {
+    cudaFuncSetAttribute(k_forward<C, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_plan(C, false, kPaccCap).total);
+    cudaFuncSetAttribute(k_adjoint<C, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_plan(C, true, 0).total);
+}
+
+template <int C, typename Fn>
+void with_ra(int ra, Fn &&fn) {
+    if (ra == 4 || C <= 4) fn(std::integral_constant<int, C>(), std::integral_constant<int, 4>());
+    else fn(std::integral_constant<int, C>(), std::integral_constant<int, 5>());
+}
+
+// Calls fn(integral_constant<C>, integral_constant<RA>) for the plan's chunk
+// size and register bits (RA = 4 or 5; chunks below 5 bits use A = C).
+template <typename Fn>
+void with_geo(int c, int ra, Fn &&fn) {
+    switch (c) {
+        case 1: with_ra<1>(ra, fn); break;
+        case 2: with_ra<2>(ra, fn); break;
+        case 3: with_ra<3>(ra, fn); break;
+        case 4: with_ra<4>(ra, fn); break;
+        case 5: with_ra<5>(ra, fn); break;
+        case 6: with_ra<6>(ra, fn); break;
+        case 7: with_ra<7>(ra, fn); break;
+        case 8: with_ra<8>(ra, fn); break;
+        case 9: with_ra<9>(ra, fn); break;
+        case 10: with_ra<10>(ra, fn); break;
+        case 11: with_ra<11>(ra, fn); break;
+        default: with_ra<12>(ra, fn); break;
+    }
 }
 
 qst_status prepare(qst_plan p, const uint8_t *basis, const int64_t *row_ptr, const uint32_t *outcome,
                    const uint32_t *shots, cudaStream_t st) {
     qst_status rc = launch(p, QST_KERNEL_PACK, st, [&] {
-        k_pack<<<1, 1024, 0, st>>>(basis, p->M, p->n, p->c, p->r, p->smax, p->plans, p->order, p->bins,
-                                   p->n_bins, p->status);
+        k_pack<<<1, 1024, 0, st>>>(basis, p->M, p->n, p->c, p->r, p->smax, p->A, p->plans, p->order,
+                                   p->bins, p->n_bins, p->status);
     });
     if (rc) return rc;
     const int warps_per_block = 8;
@@ -807,6 +1044,7 @@ void qst_params_default(qst_params *p) {
     p->chunk_qubits = 0;
     p->max_bin_settings = 0;
     p->validate = 1;
+    p->reg_bits = 0;
 }
 
 const char *qst_status_string(qst_status s) {
@@ -844,7 +1082,12 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     p->prm = prm;
     p->c = c;
     p->r = r;
-    p->A = c < kMaxA ? c : kMaxA;
+    const int ra = prm.reg_bits ? prm.reg_bits : kMaxA;
+    if (ra != 4 && ra != 5) {
+        delete p;
+        return QST_ERR_INVALID_ARG;
+    }
+    p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
     p->B = prm.norm_settings ? prm.norm_settings : M;
     cudaGetDevice(&p->device);
@@ -857,6 +1100,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         int64_t s = ((int64_t)M * ((int64_t)1 << r) * K + target - 1) / target;
         p->smax = (int)(s < 4 ? 4 : s);
     }
+    if (p->smax > kMaxBin) p->smax = kMaxBin;
     const int nkeys = ipow3(r);
     p->nb_max = (nkeys < M ? nkeys : M) + (M + p->smax - 1) / p->smax;
     const int64_t D = (int64_t)1 << n;
@@ -876,17 +1120,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc) rc = dalloc(p, &p->status, 1);
     if (!rc && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) {
-        // Sized for the largest chunk, so plans with different chunk sizes
-        // never lower each other's limit.
-        const int sf = 2 * (1 << kMaxChunk) * (int)sizeof(float2);
-        const int sa = sf + (1 << kMaxChunk) * (int)sizeof(float);
-        switch (p->A) {
-            case 1: set_smem_attrs<1>(sf, sa); break;
-            case 2: set_smem_attrs<2>(sf, sa); break;
-            case 3: set_smem_attrs<3>(sf, sa); break;
-            case 4: set_smem_attrs<4>(sf, sa); break;
-            default: set_smem_attrs<5>(sf, sa); break;
-        }
+        with_geo(p->c, p->A, [](auto cc, auto ra) { set_smem_attrs<decltype(cc)::value, decltype(ra)::value>(); });
         if (cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
     }
     if (rc) {
@@ -951,25 +1185,21 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     a.shots = shots;
     a.choff = p->choff;
     a.pacc = p_obs ? p_obs : p->pacc;
+    a.p_obs = p_obs;
     a.c_obs = c_obs;
     a.p_dense = p_dense;
     a.loss_part = p->loss_part;
     a.n = p->n;
-    a.c = p->c;
     a.r = p->r;
     a.K = p->K;
     a.invB = 1.0f / (float)p->B;
     a.eps = (float)p->prm.eps;
     const int grid = p->nb_max << p->r;
-    const int smem = 2 * (1 << p->c) * (int)sizeof(float2);
     rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
-        switch (p->A) {
-            case 1: k_forward<1><<<grid, p->T, smem, st>>>(a); break;
-            case 2: k_forward<2><<<grid, p->T, smem, st>>>(a); break;
-            case 3: k_forward<3><<<grid, p->T, smem, st>>>(a); break;
-            case 4: k_forward<4><<<grid, p->T, smem, st>>>(a); break;
-            default: k_forward<5><<<grid, p->T, smem, st>>>(a); break;
-        }
+        with_geo(p->c, p->A, [&](auto cc, auto ra) {
+            constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+            k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false, kPaccCap).total, st>>>(a);
+        });
     });
     if (rc) return rc;
     return launch(p, QST_KERNEL_LOSS, st, [&] {
@@ -1001,19 +1231,14 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     a.zbuf = p->zbuf;
     a.hpart = p->hpart;
     a.n = p->n;
-    a.c = p->c;
     a.r = p->r;
     a.K = p->K;
     const int grid = (p->nb_max << p->r) * p->K;
-    const int smem = 2 * (1 << p->c) * (int)sizeof(float2) + (1 << p->c) * (int)sizeof(float);
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
-        switch (p->A) {
-            case 1: k_adjoint<1><<<grid, p->T, smem, st>>>(a); break;
-            case 2: k_adjoint<2><<<grid, p->T, smem, st>>>(a); break;
-            case 3: k_adjoint<3><<<grid, p->T, smem, st>>>(a); break;
-            case 4: k_adjoint<4><<<grid, p->T, smem, st>>>(a); break;
-            default: k_adjoint<5><<<grid, p->T, smem, st>>>(a); break;
-        }
+        with_geo(p->c, p->A, [&](auto cc, auto ra) {
+            constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+            k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true, 0).total, st>>>(a);
+        });
     });
     if (rc) return rc;
     const float invB = 1.0f / (float)p->B;

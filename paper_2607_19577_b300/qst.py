@@ -37,7 +37,7 @@ class QSTError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm_settings", ctypes.c_int),
                 ("chunk_qubits", ctypes.c_int), ("max_bin_settings", ctypes.c_int),
-                ("validate", ctypes.c_int)]
+                ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int)]
 
 
 _lib = None
@@ -127,12 +127,13 @@ class Plan:
     """Owns a qst_plan (device workspace for one problem shape)."""
 
     def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
-                 max_bin_settings=0, validate=True):
+                 max_bin_settings=0, validate=True, reg_bits=0):
         lib = load()
         prm = _Params()
         lib.qst_params_default(ctypes.byref(prm))
         prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
         prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
+        prm.reg_bits = int(reg_bits)
         h = ctypes.c_void_p()
         _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
                "qst_plan_create")

@@ -90,6 +90,14 @@ def test_parity_forced_high_bits(chunk):
             run_oracle(inst, dense=True), dense=True)
 
 
+@pytest.mark.parametrize("n,chunk,reg_bits", [(12, 0, 4), (14, 0, 4), (16, 0, 4), (11, 7, 4), (9, 5, 4),
+                                              (9, 5, 5), (13, 9, 5)])
+def test_parity_register_layouts(n, chunk, reg_bits):
+    """Both register blockings (16 or 32 amplitudes per thread and round)."""
+    inst = synth.random_instance(n, 12 if n >= 14 else 30, 2, 1500, 900 + n + reg_bits)
+    compare(inst, run_gpu(inst, chunk_qubits=chunk, reg_bits=reg_bits), run_oracle(inst))
+
+
 @pytest.mark.parametrize("smax", [1, 2, 5])
 def test_parity_split_bins(smax):
     inst = synth.random_instance(8, 37, 3, 200, 200 + smax)
