@@ -147,7 +147,8 @@ enum {
     QST_KERNEL_ADJOINT = 4,
     QST_KERNEL_REDUCE = 5,
     QST_KERNEL_HSUM = 6,
-    QST_KERNEL_KINDS = 7
+    QST_KERNEL_EPILOGUE = 7,
+    QST_KERNEL_KINDS = 8
 };
 qst_status qst_plan_set_timing(qst_plan plan, int enable);
 qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,

@@ -47,9 +47,8 @@ constexpr int kMaxA = 5;        // register bits per round (32 amplitudes / thre
 constexpr int kMaxRounds = 3;   // 1 + ceil((kMaxChunk - kMaxA) / kMaxA)
 constexpr int kMaxTop = 4;      // high bits handled by binning (n <= 16)
 constexpr int kMaxKeys = 81;    // 3^kMaxTop
-constexpr int kMaxBin = 128;    // settings per bin (metadata staged in shared memory)
+constexpr int kMaxBin = 96;     // settings per bin (metadata staged in shared memory)
 constexpr int kStage = 1024;    // observed entries per setting staged by cp.async
-constexpr int kPaccCap = 7168;  // forward: observed entries per unit kept in shared memory
 
 // Per-setting transform plan, written by k_pack.
 struct SetPlan {
@@ -61,6 +60,7 @@ struct SetPlan {
     uint32_t rdB[kMaxRounds];  // thread bits of each round (see below)
     uint32_t key;              // base-3 basis pattern of the r high bits
     uint32_t pad;
+    uint32_t p8[kMaxRounds][8];  // 8 * phys(1 << register position j) per round (j < A; 16-B rows)
 };
 // rdA: bits [4j, 4j+4) = chunk position of register bit j (j < 5), bits
 // [20, 25) = register bits that are X/Y, bits [25, 30) = those that are Y.
@@ -101,8 +101,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Unscaled forward factors on register bit j:  X: (a,b) -> (a+b, a-b);
-// Y: (a,b) -> (a - i b, a + i b)  (rows of [[1,-i],[1,i]]).
+// Unscaled factors on register bit j, written in place (each output reuses
+// its input's registers, so branches over the per-round bit pattern need no
+// register copies at their merge points):
+//   X:  (a, b) -> (a + b, a - b)            as  a += b;  b = a - 2b
+//   Y:  (a, b) -> (a - i b, -i a + b)       as  a -= i b; b = 2b - i a
+//   Y inverse: (a, b) -> (a + i b, i a + b) as  a += i b; b = 2b + i a
+// The Y rows are those of V_Y = [[1,-i],[1,i]]/sqrt2 with the second row
+// multiplied by -i.  That per-outcome phase leaves |(V_s psi)_u|^2 unchanged,
+// and it cancels in V_s^* (c .* V_s psi) because diagonals commute, so both
+// passes compute exactly the quantities of the paper.
 template <int A>
 __device__ __forceinline__ void butterfly_fwd(float2 (&v)[1 << A], uint32_t xyf, uint32_t yf) {
 #pragma unroll
@@ -112,24 +120,27 @@ __device__ __forceinline__ void butterfly_fwd(float2 (&v)[1 << A], uint32_t xyf,
 #pragma unroll
             for (int i = 0; i < (1 << A); ++i) {
                 if ((i >> j) & 1) continue;
-                const float2 a = v[i], b = v[i | (1 << j)];
-                v[i] = make_float2(a.x + b.y, a.y - b.x);
-                v[i | (1 << j)] = make_float2(a.x - b.y, a.y + b.x);
+                float2 &a = v[i], &b = v[i | (1 << j)];
+                a.x += b.y;
+                a.y -= b.x;
+                b.x = fmaf(2.f, b.x, a.y);
+                b.y = fmaf(2.f, b.y, -a.x);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < (1 << A); ++i) {
                 if ((i >> j) & 1) continue;
-                const float2 a = v[i], b = v[i | (1 << j)];
-                v[i] = make_float2(a.x + b.x, a.y + b.y);
-                v[i | (1 << j)] = make_float2(a.x - b.x, a.y - b.y);
+                float2 &a = v[i], &b = v[i | (1 << j)];
+                a.x += b.x;
+                a.y += b.y;
+                b.x = fmaf(-2.f, b.x, a.x);
+                b.y = fmaf(-2.f, b.y, a.y);
             }
         }
     }
 }
 
-// Conjugate-transposed factors:  X: same as forward;
-// Y: (a,b) -> (a + b, i (a - b))  (rows of [[1,1],[i,-i]]).
+// Conjugate transposes of the factors above (X is its own).
 template <int A>
 __device__ __forceinline__ void butterfly_inv(float2 (&v)[1 << A], uint32_t xyf, uint32_t yf) {
 #pragma unroll
@@ -139,17 +150,21 @@ __device__ __forceinline__ void butterfly_inv(float2 (&v)[1 << A], uint32_t xyf,
 #pragma unroll
             for (int i = 0; i < (1 << A); ++i) {
                 if ((i >> j) & 1) continue;
-                const float2 a = v[i], b = v[i | (1 << j)];
-                v[i] = make_float2(a.x + b.x, a.y + b.y);
-                v[i | (1 << j)] = make_float2(b.y - a.y, a.x - b.x);
+                float2 &a = v[i], &b = v[i | (1 << j)];
+                a.x -= b.y;
+                a.y += b.x;
+                b.x = fmaf(2.f, b.x, -a.y);
+                b.y = fmaf(2.f, b.y, a.x);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < (1 << A); ++i) {
                 if ((i >> j) & 1) continue;
-                const float2 a = v[i], b = v[i | (1 << j)];
-                v[i] = make_float2(a.x + b.x, a.y + b.y);
-                v[i | (1 << j)] = make_float2(a.x - b.x, a.y - b.y);
+                float2 &a = v[i], &b = v[i | (1 << j)];
+                a.x += b.x;
+                a.y += b.y;
+                b.x = fmaf(-2.f, b.x, a.x);
+                b.y = fmaf(-2.f, b.y, a.y);
             }
         }
     }
@@ -309,6 +324,9 @@ __global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis
         }
         for (int j = nr; j < kMaxRounds; ++j) P.rdA[j] = P.rdB[j] = 0;
         P.nr = nr;
+        for (int j = 0; j < kMaxRounds; ++j)
+            for (int q = 0; q < 8; ++q)
+                P.p8[j][q] = (q < A && j < nr) ? phys(1u << ((P.rdA[j] >> (4 * q)) & 15u)) << 3 : 0u;
         plans[s] = P;
         atomicAdd(&hist[key], 1);
     }
@@ -418,21 +436,42 @@ struct Geo {
 
 __host__ __device__ constexpr int ctz_c(int t) { return (t & 1) ? 0 : 1 + ctz_c(t >> 1); }
 
-// Gray-code walk over the 2^A register elements: step t flips register bit
-// ctz(t), so each element's offset is one XOR away from the previous one.
-// Template recursion keeps every index a compile-time constant.
-template <int A, int t>
-struct GrayWalk {
-    template <typename Fn>
+// Gray-code walk over the 2^A register elements: within a chain, step t flips
+// register bit ctz(t), so each element's offset is one XOR away from the
+// previous one.  The low L register bits are walked by 2^(A-L) independent
+// chains (one per value h of the high bits), which keeps the XOR dependency
+// chains short.  Template recursion keeps every index a compile-time constant.
+template <int L, int HI, int t>
+struct GrayChain {
+    template <int A, typename Fn>
     __device__ __forceinline__ static void run(uint32_t x, const uint32_t (&P8)[A], Fn &fn) {
         constexpr int j = ctz_c(t);
         x ^= P8[j];
-        fn(std::integral_constant<int, (t ^ (t >> 1))>(), x);
-        GrayWalk<A, t + 1>::run(x, P8, fn);
+        fn(std::integral_constant<int, (HI | (t ^ (t >> 1)))>(), x);
+        GrayChain<L, HI, t + 1>::run(x, P8, fn);
     }
 };
-template <int A>
-struct GrayWalk<A, (1 << A)> {
+template <int L, int HI>
+struct GrayChain<L, HI, (1 << L)> {
+    template <int A, typename Fn>
+    __device__ __forceinline__ static void run(uint32_t, const uint32_t (&)[A], Fn &) {}
+};
+
+template <int A, int L, int h>
+struct GrayChains {
+    template <typename Fn>
+    __device__ __forceinline__ static void run(uint32_t b8, const uint32_t (&P8)[A], Fn &fn) {
+        uint32_t x = b8;
+#pragma unroll
+        for (int j = 0; j < A - L; ++j)
+            if ((h >> j) & 1) x ^= P8[L + j];
+        fn(std::integral_constant<int, (h << L)>(), x);
+        GrayChain<L, (h << L), 1>::run(x, P8, fn);
+        GrayChains<A, L, h + 1>::run(b8, P8, fn);
+    }
+};
+template <int A, int L>
+struct GrayChains<A, L, (1 << (A - L))> {
     template <typename Fn>
     __device__ __forceinline__ static void run(uint32_t, const uint32_t (&)[A], Fn &) {}
 };
@@ -447,30 +486,53 @@ struct Lay {
     uint32_t b8;          // 8 * phys(base of this thread)
     uint32_t P8[G::A];    // 8 * phys(1 << position of register bit j)
     uint32_t xyf, yf;     // which register bits are X/Y, Y
-    __device__ __forceinline__ void init(uint32_t rdA, uint32_t rdB, uint32_t tid) {
+    // lut: this setting's per-round thread-offset tables (see build_lut)
+    __device__ __forceinline__ void init(const SetPlan &P, int j, const uint32_t *lut, uint32_t tid) {
+        const uint4 lo = *reinterpret_cast<const uint4 *>(&P.p8[j][0]);
+        const uint4 hi = *reinterpret_cast<const uint4 *>(&P.p8[j][4]);
+        const uint32_t all[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int j = 0; j < G::A; ++j) P8[j] = phys(1u << ((rdA >> (4 * j)) & 15u)) << 3;
-        uint32_t base = 0;
-#pragma unroll
-        for (int b = 0; b < G::TB; ++b) base |= ((tid >> b) & 1u) << ((rdB >> (4 * b)) & 15u);
-        b8 = phys(base) << 3;
+        for (int q = 0; q < G::A; ++q) P8[q] = all[q];
+        b8 = lut[j * 32 + (tid & 15u)] ^ lut[j * 32 + 16 + ((tid >> 4) & 15u)];
+        const uint32_t rdA = P.rdA[j];
         xyf = (rdA >> 20) & 31u;
         yf = (rdA >> 25) & 31u;
     }
     // fn(integral_constant<i>, byte offset of register element i), every i once
     template <typename Fn>
     __device__ __forceinline__ void walk(Fn &&fn) const {
-        fn(std::integral_constant<int, 0>(), b8);
-        GrayWalk<G::A, 1>::run(b8, P8, fn);
+        constexpr int L = G::A < 3 ? G::A : 3;
+        GrayChains<G::A, L, 0>::run(b8, P8, fn);
     }
 };
 
 __device__ __forceinline__ float2 lds2(const unsigned char *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ void sts2(unsigned char *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 
+// Per-round thread-offset tables of one setting: for round j and each nibble
+// value v, lut[32 j + v] = 8 phys(thread bits 0..3 = v) and
+// lut[32 j + 16 + v] = 8 phys(thread bits 4..7 = v), placed at the round's
+// thread-bit positions.  phys is GF(2)-linear, so a thread's base offset is
+// the XOR of its two entries.
+template <int TB>
+__device__ __forceinline__ void build_lut(const SetPlan &P, uint32_t *lut, uint32_t tid, int T) {
+    for (int e = tid; e < kMaxRounds * 32; e += T) {
+        const int j = e >> 5, h = (e >> 4) & 1, nib = e & 15;
+        const uint32_t rdB = P.rdB[j];
+        uint32_t val = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int tb = 4 * h + b;
+            if (((nib >> b) & 1) && tb < TB) val ^= phys(1u << ((rdB >> (4 * tb)) & 15u)) << 3;
+        }
+        lut[e] = val;
+    }
+}
+
 // Chunk f of (U_h (x) I) psi_k, written to shared memory "i-major": register
 // element i of thread t (amplitude t + i 2^TB) at index i 2^TB + t.  U_h is
-// the unscaled product of the high-bit factors; Z factors select f'_j = f_j.
+// the unscaled product of the high-bit factors, with the same rows as the
+// butterflies (Z factors select f'_j = f_j).
 template <int C, int RA>
 __device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, uint32_t f,
                                              uint32_t xytop, uint32_t ytop, uint32_t tid) {
@@ -487,9 +549,9 @@ __device__ __forceinline__ void build_source(float2 *src, const float2 *__restri
             const int j = __ffs(mm) - 1;
             const uint32_t fj = (f >> j) & 1u, fpj = (fp >> j) & 1u;
             if ((ytop >> j) & 1u) {
-                if (fpj) ph += fj ? 1 : 3;
+                if (fj != fpj) ph += 3;  // Y rows [[1,-i],[-i,1]], as in the butterflies
             } else if (fj & fpj) {
-                ph += 2;
+                ph += 2;                 // X rows [[1,1],[1,-1]]
             }
         }
         return psik + ((size_t)fp << C) + tid;
@@ -530,9 +592,10 @@ __device__ __forceinline__ void build_source(float2 *src, const float2 *__restri
 // transformed chunk in the layout of the last round, described by L.
 template <int C, int RA>
 __device__ __forceinline__ void forward_rounds(float2 (&v)[Geo<C, RA>::E], Lay<C, RA> &L, const SetPlan &P,
-                                               const float2 *src, unsigned char *work, uint32_t tid) {
+                                               const uint32_t *lut, const float2 *src, unsigned char *work,
+                                               uint32_t tid) {
     using G = Geo<C, RA>;
-    L.init(P.rdA[0], P.rdB[0], tid);
+    L.init(P, 0, lut, tid);
 #pragma unroll
     for (int i = 0; i < G::E; ++i) v[i] = src[(i << G::TB) + tid];
     const int nr = P.nr;
@@ -542,16 +605,16 @@ __device__ __forceinline__ void forward_rounds(float2 (&v)[Geo<C, RA>::E], Lay<C
         __syncthreads();
         L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
         __syncthreads();
-        L.init(P.rdA[j + 1], P.rdB[j + 1], tid);
+        L.init(P, j + 1, lut, tid);
         L.walk([&](auto ic, uint32_t x) { v[decltype(ic)::value] = lds2(work + x); });
     }
 }
 
 // Shared-memory plan of the two hot kernels (bytes, for a chunk of 2^c).
 struct SmemPlan {
-    int src, work, cden, stage, plans, meta, pacc, total;
+    int src, work, cden, stage, plans, meta, lut, total;
 };
-__host__ __device__ constexpr SmemPlan smem_plan(int c, bool adjoint, int pacc_cap) {
+__host__ __device__ constexpr SmemPlan smem_plan(int c, bool adjoint) {
     SmemPlan sp{};
     sp.src = 0;
     sp.work = sp.src + (8 << c);
@@ -559,8 +622,8 @@ __host__ __device__ constexpr SmemPlan smem_plan(int c, bool adjoint, int pacc_c
     sp.stage = sp.cden + (adjoint ? (4 << c) : 0);
     sp.plans = sp.stage + 2 * kStage * (adjoint ? 8 : 4);
     sp.meta = sp.plans + kMaxBin * (int)sizeof(SetPlan);
-    sp.pacc = sp.meta + kMaxBin * (int)sizeof(SetMeta);
-    sp.total = sp.pacc + (adjoint ? 0 : 4 * pacc_cap);
+    sp.lut = sp.meta + kMaxBin * (int)sizeof(SetMeta);
+    sp.total = sp.lut + 2 * kMaxRounds * 32 * 4;
     return sp;
 }
 
@@ -573,47 +636,41 @@ struct FwdArgs {
     const int *n_bins;
     const int64_t *row_ptr;
     const uint32_t *outcome;
-    const uint32_t *count;
-    const uint32_t *shots;
     const int32_t *choff;
-    float *pacc;       // p at observed outcomes when the bin exceeds the shared accumulator
-    float *p_obs;      // optional output
-    float *c_obs;      // optional output
-    float *p_dense;    // optional [M][D]
-    double *loss_part; // [units]
+    float *ppart;      // [K][nnz]: w_k |(V_s psi_k)_u|^2 at observed outcomes
+    float *p_dense;    // optional [M][D] (accumulated with atomics; zeroed by the host)
+    int64_t nnz;
     int n, r, K;
-    float invB;
-    float eps;
 };
 
-// Forward unit = (bin, high pattern f).  Loops over the atoms and, per atom,
-// over the bin's settings; accumulates w_k 2^-m |(V_s psi_k)_u|^2 at the
-// observed outcomes of chunk f (in shared memory when they fit), then forms c
-// and the loss terms.  The next setting's outcome indices are prefetched with
-// cp.async while the current one is transformed.
+// Forward unit = (bin, high pattern f, atom k).  For every setting of the bin:
+// the chunk of V_s psi_k, then w_k 2^-m |.|^2 at the setting's observed
+// outcomes in chunk f, written to this atom's slice of the partial buffer.
+// The next setting's outcome indices are prefetched with cp.async.
 template <int C, int RA>
 __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
     using G = Geo<C, RA>;
-    constexpr SmemPlan sp = smem_plan(C, false, kPaccCap);
+    constexpr SmemPlan sp = smem_plan(C, false);
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *src = reinterpret_cast<float2 *>(smem + sp.src);
     unsigned char *work = smem + sp.work;
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem + sp.stage);
     SetPlan *plans_sm = reinterpret_cast<SetPlan *>(smem + sp.plans);
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
-    float *pacc_sm = reinterpret_cast<float *>(smem + sp.pacc);
-    __shared__ double red[kRedMax];
+    uint32_t *lut = reinterpret_cast<uint32_t *>(smem + sp.lut);
     __shared__ int total_sm;
     const uint32_t tid = threadIdx.x;
     const int unit = blockIdx.x;
-    const int bin = unit >> a.r;
-    const uint32_t f = unit & ((1u << a.r) - 1u);
+    const int k = unit % a.K;
+    const int rest = unit / a.K;
+    const uint32_t f = rest & ((1u << a.r) - 1u);
+    const int bin = rest >> a.r;
     if (bin >= *a.n_bins) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
     constexpr uint32_t cmask = G::N - 1;
+    constexpr int LUTW = kMaxRounds * 32;
     stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, plans_sm, meta_sm, &total_sm);
-    const bool in_sm = total_sm <= kPaccCap;
     const int bcount = b.count;
     const uint32_t *outcome = a.outcome;
     auto issue = [=](int si) {
@@ -625,63 +682,77 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
         }
         cp_async_commit();
     };
-    for (int k = 0; k < a.K; ++k) {
-        const float wk = a.w[k];
-        build_source<C, RA>(src, a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
-        issue(0);
-        __syncthreads();
-        for (int si = 0; si < b.count; ++si) {
-            issue(si + 1);
-            const SetPlan &P = plans_sm[si];
-            const SetMeta mt = meta_sm[si];
-            float2 v[G::E];
-            Lay<C, RA> L;
-            forward_rounds<C, RA>(v, L, P, src, work, tid);
-            cp_async_wait1();
-            __syncthreads();
-            L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
-            __syncthreads();
-            const float sc = wk * mt.cs;
-            const uint32_t *st = stage + (si & 1) * kStage;
-            for (int j = tid; j < mt.cnt; j += G::T) {
-                const uint32_t u = (j < kStage ? st[j] : a.outcome[mt.lo + j]) & cmask;
-                const float2 ph = lds2(work + (phys(u) << 3));
-                const float val = sc * (ph.x * ph.x + ph.y * ph.y);
-                float *pp = in_sm ? pacc_sm + mt.off + j : a.pacc + mt.lo + j;
-                *pp = (k == 0) ? val : *pp + val;
-            }
-            if (a.p_dense) {
-                const int s = a.order[b.start + si];
-                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
-                for (uint32_t u = tid; u <= cmask; u += G::T) {
-                    const float2 ph = lds2(work + (phys(u) << 3));
-                    const float val = sc * (ph.x * ph.x + ph.y * ph.y);
-                    pd[u] = (k == 0) ? val : pd[u] + val;
-                }
-            }
-            __syncthreads();  // stage buffer and work are reused by the next setting
-        }
-        cp_async_wait0();
-        __syncthreads();
-    }
-    // epilogue: likelihood ratio and loss terms at this unit's observed outcomes
-    double lsum = 0.0;
-    for (int si = 0; si < b.count; ++si) {
+    const float wk = a.w[k];
+    float *pk = a.ppart + (size_t)k * a.nnz;
+    issue(0);
+    build_source<C, RA>(src, a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
+    if (bcount > 0) build_lut<G::TB>(plans_sm[0], lut, tid, G::T);
+    __syncthreads();
+    for (int si = 0; si < bcount; ++si) {
+        issue(si + 1);
+        const SetPlan &P = plans_sm[si];
         const SetMeta mt = meta_sm[si];
-        const int s = a.order[b.start + si];
-        const float ns = (float)a.shots[s];
+        float2 v[G::E];
+        Lay<C, RA> L;
+        forward_rounds<C, RA>(v, L, P, lut + (si & 1) * LUTW, src, work, tid);
+        cp_async_wait1();
+        __syncthreads();
+        L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
+        __syncthreads();
+        const float sc = wk * mt.cs;
+        const uint32_t *st = stage + (si & 1) * kStage;
         for (int j = tid; j < mt.cnt; j += G::T) {
-            const int64_t i = (int64_t)mt.lo + j;
-            const float p = in_sm ? pacc_sm[mt.off + j] : a.pacc[i];
-            const float pi = p * a.invB;
-            const float pihat = (float)a.count[i] * a.invB / ns;
-            if (a.c_obs) a.c_obs[i] = pihat / (pi + a.eps);
-            if (a.p_obs) a.p_obs[i] = p;
-            lsum -= (double)pihat * (double)logf(pi + a.eps);
+            const uint32_t u = (j < kStage ? st[j] : outcome[mt.lo + j]) & cmask;
+            const float2 ph = lds2(work + (phys(u) << 3));
+            pk[mt.lo + j] = sc * (ph.x * ph.x + ph.y * ph.y);
+        }
+        if (a.p_dense) {
+            const int s = a.order[b.start + si];
+            float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
+            for (uint32_t u = tid; u <= cmask; u += G::T) {
+                const float2 ph = lds2(work + (phys(u) << 3));
+                atomicAdd(pd + u, sc * (ph.x * ph.x + ph.y * ph.y));
+            }
+        }
+        if (si + 1 < bcount) build_lut<G::TB>(plans_sm[si + 1], lut + ((si + 1) & 1) * LUTW, tid, G::T);
+        __syncthreads();  // stage buffer and work are reused by the next setting
+    }
+    cp_async_wait0();
+}
+
+// Forward epilogue, one warp per setting: p = sum_k of the atom partials
+// (fixed order), pi = p / B, c = pihat / (pi + eps) and the loss terms
+// -pihat log(pi + eps) (Eqs. qst-loss, likelihood-ratio-vector).  Per-block
+// FP64 loss partials are summed by k_loss.
+__global__ void __launch_bounds__(256) k_fwd_epilogue(const float *__restrict__ ppart, const int64_t *__restrict__ row_ptr,
+                                                      const uint32_t *__restrict__ count,
+                                                      const uint32_t *__restrict__ shots,
+                                                      int M, int K, int64_t nnz, float invB, float eps,
+                                                      float *__restrict__ p_obs, float *__restrict__ c_obs,
+                                                      double *__restrict__ loss_part) {
+    __shared__ double red[kRedMax];
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double lsum = 0.0;
+    if (s < M) {
+        const int64_t lo = row_ptr[s], hi = row_ptr[s + 1];
+        // rows flagged malformed by the validation are skipped (their offsets were emptied)
+        const bool ok = lo >= 0 && hi >= lo && hi <= nnz && shots[s] > 0u;
+        if (ok) {
+            const float ns = (float)shots[s];
+            for (int64_t i = lo + lane; i < hi; i += 32) {
+                float p = 0.f;
+                for (int k = 0; k < K; ++k) p += ppart[(size_t)k * nnz + i];
+                const float pi = p * invB;
+                const float pihat = (float)count[i] * invB / ns;
+                if (c_obs) c_obs[i] = pihat / (pi + eps);
+                if (p_obs) p_obs[i] = p;
+                lsum -= (double)pihat * (double)logf(pi + eps);
+            }
         }
     }
     const double t = block_sum<double>(lsum, red);
-    if (tid == 0) a.loss_part[unit] = t;
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
 }
 
 struct AdjArgs {
@@ -695,7 +766,6 @@ struct AdjArgs {
     const float *c_obs;
     const int32_t *choff;
     float2 *zbuf;    // [bins][K][D]
-    float *hpart;    // [units]
     int n, r, K;
 };
 
@@ -708,7 +778,7 @@ struct AdjArgs {
 template <int C, int RA>
 __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
     using G = Geo<C, RA>;
-    constexpr SmemPlan sp = smem_plan(C, true, 0);
+    constexpr SmemPlan sp = smem_plan(C, true);
     extern __shared__ __align__(16) unsigned char smem[];
     const float2 *src = reinterpret_cast<const float2 *>(smem + sp.src);
     unsigned char *work = smem + sp.work;
@@ -717,7 +787,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
     float *stage_c = reinterpret_cast<float *>(smem + sp.stage + 2 * kStage * 4);
     SetPlan *plans_sm = reinterpret_cast<SetPlan *>(smem + sp.plans);
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
-    __shared__ float red[kRedMax];
+    uint32_t *lut = reinterpret_cast<uint32_t *>(smem + sp.lut);
     __shared__ int total_sm;
     const uint32_t tid = threadIdx.x;
     const int unit = blockIdx.x;
@@ -729,6 +799,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
     constexpr uint32_t cmask = G::N - 1;
+    constexpr int LUTW = kMaxRounds * 32;
     float *cden = reinterpret_cast<float *>(cdb);
     for (uint32_t u = tid; u <= cmask; u += G::T) cden[u] = 0.f;
     stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, plans_sm, meta_sm, &total_sm);
@@ -762,25 +833,25 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
     };
     issue(0);
     build_source<C, RA>(const_cast<float2 *>(src), a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
+    if (bcount > 0) build_lut<G::TB>(plans_sm[0], lut, tid, G::T);
     cp_async_wait0();
-    __syncthreads();  // c buffer zeroed, source built
-    if (b.count > 0) scatter(0, false);
+    __syncthreads();  // c buffer zeroed, source built, round tables ready
+    if (bcount > 0) scatter(0, false);
     float2 z[G::E];
 #pragma unroll
     for (int i = 0; i < G::E; ++i) z[i] = make_float2(0.f, 0.f);
-    float hacc = 0.f;
     for (int si = 0; si < b.count; ++si) {
         issue(si + 1);
         const SetPlan &P = plans_sm[si];
         const int nr = P.nr;
+        const uint32_t *lt = lut + (si & 1) * LUTW;
         float2 v[G::E];
         Lay<C, RA> L;
-        forward_rounds<C, RA>(v, L, P, src, work, tid);
+        forward_rounds<C, RA>(v, L, P, lt, src, work, tid);
         if (nr == 1) __syncthreads();  // this setting's c scatter is visible
         L.walk([&](auto ic, uint32_t x) {
             constexpr int i = decltype(ic)::value;
             const float cc = *reinterpret_cast<const float *>(cdb + (x >> 1));
-            hacc += cc * (v[i].x * v[i].x + v[i].y * v[i].y);
             v[i].x *= cc;
             v[i].y *= cc;
         });
@@ -790,7 +861,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
             __syncthreads();
             L.walk([&](auto ic, uint32_t x) { sts2(work + x, v[decltype(ic)::value]); });
             __syncthreads();
-            L.init(P.rdA[j - 1], P.rdB[j - 1], tid);
+            L.init(P, j - 1, lt, tid);
             L.walk([&](auto ic, uint32_t x) { v[decltype(ic)::value] = lds2(work + x); });
         }
 #pragma unroll
@@ -800,15 +871,14 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
         }
         if (nr == 1) __syncthreads();  // every thread is done reading the c buffer
         scatter(si, true);
+        if (si + 1 < bcount) build_lut<G::TB>(plans_sm[si + 1], lut + ((si + 1) & 1) * LUTW, tid, G::T);
         cp_async_wait0();
-        __syncthreads();  // cleared before the next scatter; stage free for reuse
+        __syncthreads();  // cleared before the next scatter; stage free for reuse; next tables ready
         if (si + 1 < b.count) scatter(si + 1, false);
     }
     float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << C);
 #pragma unroll
     for (int i = 0; i < G::E; ++i) zo[tid + (i << G::TB)] = z[i];
-    const float t = block_sum<float>(hacc, red);
-    if (tid == 0) a.hpart[unit] = t;
 }
 
 // grad_k[f, l] = -(w_k / B) sum_bins (U_h^* z_{bin,k})[f, l]: the high-bit
@@ -816,7 +886,8 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
 template <int R>
 __global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf, const Bin *__restrict__ bins,
                                                 const int *__restrict__ n_bins, const float *__restrict__ w,
-                                                float2 *__restrict__ grad, int n, int c, int K, float invB) {
+                                                const float2 *__restrict__ psi, float2 *__restrict__ grad,
+                                                double *__restrict__ hdot, int n, int c, int K, float invB) {
     constexpr int F = 1 << R;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)K << c;
@@ -848,29 +919,36 @@ __global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf,
     }
     const float sc = -w[k] * invB;
     float2 *gp = grad + (size_t)k * D + ul;
+    const float2 *pp = psi + (size_t)k * D + ul;
+    double hd = 0.0;  // Re <psi_k | B G psi_k> over this thread's amplitudes
 #pragma unroll
-    for (int f = 0; f < F; ++f) gp[(size_t)f << c] = make_float2(sc * acc[f].x, sc * acc[f].y);
+    for (int f = 0; f < F; ++f) {
+        gp[(size_t)f << c] = make_float2(sc * acc[f].x, sc * acc[f].y);
+        const float2 q = pp[(size_t)f << c];
+        hd += (double)q.x * (double)acc[f].x + (double)q.y * (double)acc[f].y;
+    }
+    hdot[idx] = hd;
 }
 
-// grad_w_k = -(1/B) sum over (bin, f) units of the h partial sums (FP64).
-__global__ void __launch_bounds__(256) k_hsum(const float *__restrict__ hpart, const int *__restrict__ n_bins,
-                                              int r, int K, float invB, float *__restrict__ grad_w) {
+// grad_w_k = -h_k with h_k = a(psi_k)^T c = <psi_k | G psi_k> (Eqs. weight-gradient,
+// atom-response): the FP64 sum of the reduction kernel's per-thread partials.
+__global__ void __launch_bounds__(256) k_hsum(const double *__restrict__ hdot, int c, float invB,
+                                              float *__restrict__ grad_w) {
     __shared__ double red[kRedMax];
     const int k = blockIdx.x;
-    const int units = *n_bins << r;
+    const double *hp = hdot + ((size_t)k << c);
     double s = 0.0;
-    for (int u = threadIdx.x; u < units; u += blockDim.x) s += (double)hpart[(size_t)u * K + k];
+    for (int u = threadIdx.x; u < (1 << c); u += blockDim.x) s += hp[u];
     const double t = block_sum<double>(s, red);
     if (threadIdx.x == 0) grad_w[k] = (float)(-t * (double)invB);
 }
 
-// loss = sum of the forward units' partial sums (FP64, fixed order).
-__global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_part, const int *__restrict__ n_bins,
-                                              int r, double *__restrict__ loss, int *__restrict__ status) {
+// loss = sum of the forward epilogue's per-block partial sums (FP64, fixed order).
+__global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_part, int parts,
+                                              double *__restrict__ loss, int *__restrict__ status) {
     __shared__ double red[kRedMax];
-    const int units = *n_bins << r;
     double s = 0.0;
-    for (int u = threadIdx.x; u < units; u += blockDim.x) s += loss_part[u];
+    for (int u = threadIdx.x; u < parts; u += blockDim.x) s += loss_part[u];
     const double t = block_sum<double>(s, red);
     if (threadIdx.x == 0) {
         if (loss) *loss = t;
@@ -904,12 +982,12 @@ struct qst_plan_s {
     Bin *bins = nullptr;
     int *n_bins = nullptr;
     int32_t *choff = nullptr;
-    float *pacc = nullptr;
+    float *ppart = nullptr;
     double *loss_part = nullptr;
+    int loss_parts = 0;
     float2 *zbuf = nullptr;
-    float *hpart = nullptr;
+    double *hdot = nullptr;
     int *status = nullptr;
-    float *c_internal = nullptr;
     int64_t ws_bytes = 0;
     // host-buffer path (allocated on first use)
     void *h_dev = nullptr;
@@ -987,9 +1065,9 @@ bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 template <int C, int RA>
 void set_smem_attrs() {
     cudaFuncSetAttribute(k_forward<C, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_plan(C, false, kPaccCap).total);
+                         smem_plan(C, false).total);
     cudaFuncSetAttribute(k_adjoint<C, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_plan(C, true, 0).total);
+                         smem_plan(C, true).total);
 }
 
 template <int C, typename Fn>
@@ -1104,19 +1182,17 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     const int nkeys = ipow3(r);
     p->nb_max = (nkeys < M ? nkeys : M) + (M + p->smax - 1) / p->smax;
     const int64_t D = (int64_t)1 << n;
-    const int64_t units_f = (int64_t)p->nb_max << r;
-    const int64_t units_a = units_f * K;
+    p->loss_parts = (M + 7) / 8;  // forward epilogue: one warp per setting, 8 warps per block
     qst_status rc = QST_OK;
     if (!rc) rc = dalloc(p, &p->plans, M);
     if (!rc) rc = dalloc(p, &p->order, M);
     if (!rc) rc = dalloc(p, &p->bins, p->nb_max);
     if (!rc) rc = dalloc(p, &p->n_bins, 1);
     if (!rc) rc = dalloc(p, &p->choff, (size_t)M * ((1 << r) + 1));
-    if (!rc) rc = dalloc(p, &p->pacc, nnz);
-    if (!rc) rc = dalloc(p, &p->c_internal, nnz);
-    if (!rc) rc = dalloc(p, &p->loss_part, units_f);
+    if (!rc) rc = dalloc(p, &p->ppart, (size_t)K * nnz);
+    if (!rc) rc = dalloc(p, &p->loss_part, p->loss_parts);
     if (!rc) rc = dalloc(p, &p->zbuf, (size_t)p->nb_max * K * D);
-    if (!rc) rc = dalloc(p, &p->hpart, units_a);
+    if (!rc) rc = dalloc(p, &p->hdot, (size_t)K << c);
     if (!rc) rc = dalloc(p, &p->status, 1);
     if (!rc && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) {
@@ -1138,11 +1214,10 @@ qst_status qst_plan_destroy(qst_plan p) {
     cudaFree(p->bins);
     cudaFree(p->n_bins);
     cudaFree(p->choff);
-    cudaFree(p->pacc);
-    cudaFree(p->c_internal);
+    cudaFree(p->ppart);
     cudaFree(p->loss_part);
     cudaFree(p->zbuf);
-    cudaFree(p->hpart);
+    cudaFree(p->hdot);
     cudaFree(p->status);
     cudaFree(p->h_dev);
     for (auto &tl : p->pending) {
@@ -1172,6 +1247,8 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     cudaStream_t st = (cudaStream_t)stream;
     qst_status rc = prepare(p, basis, row_ptr, outcome, shots, st);
     if (rc) return rc;
+    if (p_dense && cudaMemsetAsync(p_dense, 0, (size_t)p->M * ((size_t)1 << p->n) * sizeof(float), st) != cudaSuccess)
+        return QST_ERR_CUDA;
     FwdArgs a;
     a.psi = reinterpret_cast<const float2 *>(psi);
     a.w = w;
@@ -1181,29 +1258,30 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     a.n_bins = p->n_bins;
     a.row_ptr = row_ptr;
     a.outcome = outcome;
-    a.count = count;
-    a.shots = shots;
     a.choff = p->choff;
-    a.pacc = p_obs ? p_obs : p->pacc;
-    a.p_obs = p_obs;
-    a.c_obs = c_obs;
+    a.ppart = p->ppart;
     a.p_dense = p_dense;
-    a.loss_part = p->loss_part;
+    a.nnz = p->nnz;
     a.n = p->n;
     a.r = p->r;
     a.K = p->K;
-    a.invB = 1.0f / (float)p->B;
-    a.eps = (float)p->prm.eps;
-    const int grid = p->nb_max << p->r;
+    const int grid = (p->nb_max << p->r) * p->K;
     rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
         with_geo(p->c, p->A, [&](auto cc, auto ra) {
             constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-            k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false, kPaccCap).total, st>>>(a);
+            k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
         });
     });
     if (rc) return rc;
+    const float invB = 1.0f / (float)p->B;
+    const int egrid = p->loss_parts;
+    rc = launch(p, QST_KERNEL_EPILOGUE, st, [&] {
+        k_fwd_epilogue<<<egrid, 256, 0, st>>>(p->ppart, row_ptr, count, shots, p->M, p->K, p->nnz, invB,
+                                              (float)p->prm.eps, p_obs, c_obs, p->loss_part);
+    });
+    if (rc) return rc;
     return launch(p, QST_KERNEL_LOSS, st, [&] {
-        k_loss<<<1, 256, 0, st>>>(p->loss_part, p->n_bins, p->r, loss, p->status);
+        k_loss<<<1, 256, 0, st>>>(p->loss_part, p->loss_parts, loss, p->status);
     });
 }
 
@@ -1229,7 +1307,6 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     a.c_obs = c_obs;
     a.choff = p->choff;
     a.zbuf = p->zbuf;
-    a.hpart = p->hpart;
     a.n = p->n;
     a.r = p->r;
     a.K = p->K;
@@ -1237,7 +1314,7 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
         with_geo(p->c, p->A, [&](auto cc, auto ra) {
             constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-            k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true, 0).total, st>>>(a);
+            k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true).total, st>>>(a);
         });
     });
     if (rc) return rc;
@@ -1247,16 +1324,16 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     float2 *g = reinterpret_cast<float2 *>(grad_psi);
     rc = launch(p, QST_KERNEL_REDUCE, st, [&] {
         switch (p->r) {
-            case 0: k_reduce<0><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
-            case 1: k_reduce<1><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
-            case 2: k_reduce<2><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
-            case 3: k_reduce<3><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
-            default: k_reduce<4><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, g, p->n, p->c, p->K, invB); break;
+            case 0: k_reduce<0><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
+            case 1: k_reduce<1><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
+            case 2: k_reduce<2><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
+            case 3: k_reduce<3><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
+            default: k_reduce<4><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
         }
     });
     if (rc || !grad_w) return rc;
     return launch(p, QST_KERNEL_HSUM, st, [&] {
-        k_hsum<<<p->K, 256, 0, st>>>(p->hpart, p->n_bins, p->r, p->K, invB, grad_w);
+        k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invB, grad_w);
     });
 }
 
