@@ -43,7 +43,8 @@ typedef enum qst_status {
     QST_ERR_UNSUPPORTED = 2, /* size outside what this build handles (see qst_plan_create) */
     QST_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     QST_ERR_NO_MEMORY = 4,   /* workspace allocation failed */
-    QST_ERR_DEVICE = 5       /* qst_plan_status found device-side error bits */
+    QST_ERR_DEVICE = 5,      /* qst_plan_status found device-side error bits */
+    QST_ERR_SCRATCH_TOO_SMALL = 6 /* qst_adjoint_noalloc: problem needs more than its scratch */
 } qst_status;
 
 /* Bits of the device status word. */
@@ -156,6 +157,39 @@ qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,
 qst_status qst_plan_reset_stats(qst_plan plan);
 /* Total kernel launches issued by this plan since creation / last reset. */
 qst_status qst_plan_launch_count(qst_plan plan, int64_t *count);
+
+/*
+ * Adjoint without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc.  Examples are
+ * code running under an allocator it does not own (a framework's caching
+ * pool, a sandbox that forbids raw device allocation) and loops that must not
+ * pay cudaMalloc's implicit device synchronisation.
+ *
+ * It computes exactly what qst_adjoint computes (same arguments and outputs;
+ * psi, w, basis, CSR, c_obs, grad_psi, grad_w are caller-owned device memory).
+ * The shape and params take the place of a plan, and device_status is a
+ * caller-owned device int.  The call zeroes it, then device-side data checks
+ * OR their QST_DEV_* bits into it.  All workspace comes from one file-scope
+ * device array of QST_NOALLOC_SCRATCH_BYTES, which every GPU that loads the
+ * library holds until the process exits.  The call uses the largest bins
+ * (fewest z buffers) and returns QST_ERR_SCRATCH_TOO_SMALL, with a message
+ * on stderr, when the problem needs more.  Roughly, the workspace is
+ * (bins) x K x 2^n x 8 bytes plus a few bytes per setting.  For example,
+ * n = 12, M = 2000, K = 8 fits, while n = 16, K = 16 does not.
+ *
+ * The first call on each device looks up the array's device address and sets
+ * kernel attributes, so make that first call before any stream capture.
+ * Every call shares the one array, and it keeps the last call's contents.
+ * Calls that overlap on the GPU (other streams, other host threads) race on
+ * it, so serialise them.
+ */
+#define QST_NOALLOC_SCRATCH_BYTES (32u << 20)
+qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz,
+                               const qst_params *params, const float *psi,
+                               const float *w, const uint8_t *basis,
+                               const int64_t *row_ptr, const uint32_t *outcome,
+                               const float *c_obs, float *grad_psi,
+                               float *grad_w, int *device_status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -1133,6 +1134,7 @@ const char *qst_status_string(qst_status s) {
         case QST_ERR_CUDA: return "CUDA error";
         case QST_ERR_NO_MEMORY: return "out of device memory";
         case QST_ERR_DEVICE: return "device-side error";
+        case QST_ERR_SCRATCH_TOO_SMALL: return "problem exceeds the no-allocation scratch";
     }
     return "unknown status";
 }
@@ -1438,3 +1440,117 @@ qst_status qst_plan_launch_count(qst_plan p, int64_t *count) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------- adjoint without allocation
+//
+// qst_adjoint_noalloc serves callers that cannot call cudaMalloc: code running
+// under an allocator it does not own (a framework's caching pool, a sandbox
+// that forbids raw device allocation), or loops that must not trigger
+// cudaMalloc's implicit device synchronisation.  Its workspace is this
+// file-scope device array instead of a plan's cudaMalloc'd buffers.  Every GPU
+// that loads the library holds the array until the process exits.
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QST_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up (cudaGetSymbolAddress, with that device current) and
+// sets the kernels' shared-memory limits; later calls reuse the address.
+qst_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return QST_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return QST_ERR_CUDA;
+        }
+        for (int c = 1; c <= kMaxChunk; ++c)
+            for (int ra = 4; ra <= 5; ++ra)
+                with_geo(c, ra, [](auto cc, auto rr) { set_smem_attrs<decltype(cc)::value, decltype(rr)::value>(); });
+        if (cudaGetLastError() != cudaSuccess) return QST_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return QST_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz, const qst_params *params,
+                                          const float *psi, const float *w, const uint8_t *basis,
+                                          const int64_t *row_ptr, const uint32_t *outcome, const float *c_obs,
+                                          float *grad_psi, float *grad_w, int *device_status, void *stream) {
+    if (n < 1 || M < 1 || K < 1 || nnz < 0 || !device_status) return QST_ERR_INVALID_ARG;
+    if (nnz > (int64_t)M << n) return QST_ERR_INVALID_ARG;
+    qst_params prm;
+    qst_params_default(&prm);
+    if (params) prm = *params;
+    if (!(prm.eps >= 0.0) || prm.norm_settings < 0 || prm.max_bin_settings < 0) return QST_ERR_INVALID_ARG;
+    const int c = prm.chunk_qubits ? prm.chunk_qubits : (n < kMaxChunk ? n : kMaxChunk);
+    if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
+    const int r = n - c;
+    if (r > kMaxTop || K > 4096 || M > (1 << 24) || nnz > ((int64_t)1 << 31) - 1) return QST_ERR_UNSUPPORTED;
+    const int ra = prm.reg_bits ? prm.reg_bits : kMaxA;
+    if (ra != 4 && ra != 5) return QST_ERR_INVALID_ARG;
+    // Fewest bins (largest bins) keep the z buffer small.
+    const int smax = prm.max_bin_settings ? (prm.max_bin_settings < kMaxBin ? prm.max_bin_settings : kMaxBin)
+                                          : kMaxBin;
+    const int nkeys = ipow3(r);
+    const int nb_max = (nkeys < M ? nkeys : M) + (M + smax - 1) / smax;
+    const size_t D = (size_t)1 << n;
+    // scratch layout
+    size_t off = 0;
+    const size_t o_nbins = off; off += align256(sizeof(int));
+    const size_t o_bins = off; off += align256((size_t)nb_max * sizeof(Bin));
+    const size_t o_plans = off; off += align256((size_t)M * sizeof(SetPlan));
+    const size_t o_order = off; off += align256((size_t)M * sizeof(int32_t));
+    const size_t o_choff = off; off += align256((size_t)M * ((1u << r) + 1) * sizeof(int32_t));
+    const size_t o_hdot = off; off += align256(((size_t)K << c) * sizeof(double));
+    const size_t o_zbuf = off; off += align256((size_t)nb_max * K * D * sizeof(float2));
+    if (off > (size_t)QST_NOALLOC_SCRATCH_BYTES) {
+        fprintf(stderr, "qst_adjoint_noalloc: needs %zu bytes of workspace, the scratch holds %u\n", off,
+                (unsigned)QST_NOALLOC_SCRATCH_BYTES);
+        return QST_ERR_SCRATCH_TOO_SMALL;
+    }
+    unsigned char *base = nullptr;
+    qst_status rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    // The device status word is the caller's; it must start at zero.
+    if (cudaMemsetAsync(device_status, 0, sizeof(int), st) != cudaSuccess) return QST_ERR_CUDA;
+    // A plan object on the stack whose workspace pointers point into the
+    // scratch; qst_adjoint then runs unchanged and allocates nothing.
+    qst_plan_s tmp;
+    tmp.n = n;
+    tmp.M = M;
+    tmp.K = K;
+    tmp.nnz = nnz;
+    tmp.prm = prm;
+    tmp.c = c;
+    tmp.r = r;
+    tmp.A = c < ra ? c : ra;
+    tmp.T = 1 << (c - tmp.A);
+    tmp.B = prm.norm_settings ? prm.norm_settings : M;
+    tmp.smax = smax;
+    tmp.nb_max = nb_max;
+    cudaGetDevice(&tmp.device);
+    tmp.n_bins = reinterpret_cast<int *>(base + o_nbins);
+    tmp.bins = reinterpret_cast<Bin *>(base + o_bins);
+    tmp.plans = reinterpret_cast<SetPlan *>(base + o_plans);
+    tmp.order = reinterpret_cast<int32_t *>(base + o_order);
+    tmp.choff = reinterpret_cast<int32_t *>(base + o_choff);
+    tmp.hdot = reinterpret_cast<double *>(base + o_hdot);
+    tmp.zbuf = reinterpret_cast<float2 *>(base + o_zbuf);
+    tmp.status = device_status;
+    // tmp owns nothing: its workspace pointers are views of the scratch array
+    return qst_adjoint(&tmp, psi, w, basis, row_ptr, outcome, c_obs, grad_psi, grad_w, stream);
+}

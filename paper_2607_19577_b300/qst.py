@@ -66,9 +66,11 @@ def load():
         lib.qst_plan_kernel_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(f64), i32]
         lib.qst_plan_reset_stats.argtypes = [P]
         lib.qst_plan_launch_count.argtypes = [P, ctypes.POINTER(i64)]
+        lib.qst_adjoint_noalloc.argtypes = [i32, i32, i32, i64, ctypes.POINTER(_Params)] + [P] * 9 + [P]
         for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_forward",
                      "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
-                     "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count"]:
+                     "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
+                     "qst_adjoint_noalloc"]:
             getattr(lib, name).restype = i32
         _lib = lib
     return _lib
@@ -271,6 +273,31 @@ class QSTLoss(torch.autograd.Function):
         grad_psi, grad_w = ctx.plan.adjoint(psi, w, ctx.data, c_obs)
         g32 = g.to(torch.float32)
         return 2.0 * g32 * grad_psi, g32 * grad_w, None, None
+
+
+QST_ERR_SCRATCH_TOO_SMALL = 6
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def adjoint_noalloc(psi, w, d: Data, c_obs, grad_psi, grad_w, device_status, params=None):
+    """qst_adjoint_noalloc: the adjoint for callers that cannot allocate device
+    memory (their workspace would otherwise come from cudaMalloc).  Every
+    argument is a caller-owned CUDA tensor; device_status is an int32 [1]
+    tensor that receives the device-side data-check bits.  Returns the status
+    code (QST_ERR_SCRATCH_TOO_SMALL when the problem needs more than the
+    library's fixed scratch)."""
+    K, D = psi.shape
+    n = D.bit_length() - 1
+    prm = None
+    if params is not None:
+        prm = _Params()
+        load().qst_params_default(ctypes.byref(prm))
+        for k, v in params.items():
+            setattr(prm, k, v)
+    return load().qst_adjoint_noalloc(int(n), int(d.M), int(K), int(d.nnz),
+                                      ctypes.byref(prm) if prm is not None else None,
+                                      _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr), _ptr(d.outcome),
+                                      _ptr(c_obs), _ptr(grad_psi), _ptr(grad_w), _ptr(device_status), _stream())
 
 
 def qst_loss(psi, w, plan: Plan, data: Data):
