@@ -112,6 +112,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_hash():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2607_19577_b300", "csrc", "qst.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()
+
+
 def algorithmic_ops(basis, K, D):
     """FP32 lane operations (FADD/FMUL/FFMA each 1) of the plain butterfly method:
     forward 2 m_s + 4 and adjoint 4 m_s + 8 per amplitude, m_s = X/Y qubits of s."""
@@ -256,7 +262,10 @@ def run_ours(args):
     prof = os.path.join(ROOT, "profiles", "adjoint_traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
+            rec = json.load(open(prof))
+            # counters only count for the kernel source they were taken on
+            if rec.get("source_sha256") == kernel_source_hash() and rec.get("workload") == args.workload:
+                traffic = rec.get("bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",

@@ -44,8 +44,8 @@
 namespace {
 
 constexpr int kMaxChunk = 12;   // chunk bits transformed on-chip
-constexpr int kMaxA = 5;        // register bits per round (32 amplitudes / thread)
-constexpr int kMaxRounds = 3;   // 1 + ceil((kMaxChunk - kMaxA) / kMaxA)
+constexpr int kMaxRounds = 3;   // 1 + ceil((kMaxChunk - A) / A) for A = 4, 5
+constexpr int kDefaultRegBits = 4;  // 16 amplitudes per thread and round (measured faster than 32)
 constexpr int kMaxTop = 4;      // high bits handled by binning (n <= 16)
 constexpr int kMaxKeys = 81;    // 3^kMaxTop
 constexpr int kMaxBin = 96;     // settings per bin (metadata staged in shared memory)
@@ -1162,7 +1162,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     p->prm = prm;
     p->c = c;
     p->r = r;
-    const int ra = prm.reg_bits ? prm.reg_bits : kMaxA;
+    const int ra = prm.reg_bits ? prm.reg_bits : kDefaultRegBits;
     if (ra != 4 && ra != 5) {
         delete p;
         return QST_ERR_INVALID_ARG;
@@ -1499,7 +1499,7 @@ extern "C" qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz, cons
     if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
     const int r = n - c;
     if (r > kMaxTop || K > 4096 || M > (1 << 24) || nnz > ((int64_t)1 << 31) - 1) return QST_ERR_UNSUPPORTED;
-    const int ra = prm.reg_bits ? prm.reg_bits : kMaxA;
+    const int ra = prm.reg_bits ? prm.reg_bits : kDefaultRegBits;
     if (ra != 4 && ra != 5) return QST_ERR_INVALID_ARG;
     // Fewest bins (largest bins) keep the z buffer small.
     const int smax = prm.max_bin_settings ? (prm.max_bin_settings < kMaxBin ? prm.max_bin_settings : kMaxBin)
