@@ -149,7 +149,9 @@ enum {
     QST_KERNEL_REDUCE = 5,
     QST_KERNEL_HSUM = 6,
     QST_KERNEL_EPILOGUE = 7,
-    QST_KERNEL_KINDS = 8
+    QST_KERNEL_REFACTOR = 8,
+    QST_KERNEL_STEP = 9,
+    QST_KERNEL_KINDS = 10
 };
 qst_status qst_plan_set_timing(qst_plan plan, int enable);
 qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,
@@ -157,6 +159,70 @@ qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,
 qst_status qst_plan_reset_stats(qst_plan plan);
 /* Total kernel launches issued by this plan since creation / last reset. */
 qst_status qst_plan_launch_count(qst_plan plan, int64_t *count);
+
+/*
+ * Euclidean projection onto the probability simplex followed by the
+ * truncation map P_tau (Eq. coefficient-update's proj_Delta; Eq.
+ * truncation-map): beta = max(v - theta, 0) with theta chosen so that
+ * sum beta = 1 (sort-based exact method), then entries with beta_r <= tau are
+ * dropped and the rest renormalised; if none survives, the largest is kept.
+ *   v [K] double (device, read), 1 <= K <= 1024
+ *   beta [K] double (device, written): renormalised kept weights, 0 elsewhere
+ *   keep [K] int (device, written): kept indices in ascending order, first *K_out valid
+ *   K_out [1] int (device, written)
+ * FP64 throughout; one CTA.  Needs no plan and no workspace.
+ */
+qst_status qst_simplex_project(const double *v, int K, double tau, double *beta,
+                               int *keep, int *K_out, void *stream);
+
+/*
+ * Exact spectral refactorisation of rho = Psi diag(w) Psi^*: the paper's
+ * spectral step (Sec. III-C, Eqs. ritz-pairs, spectral-candidates) with
+ * eta_rho = 0, where its Ritz pairs are exact eigenpairs of rho_t.  Through the
+ * K x K Gram matrix H = diag(sqrt w) Psi^* Psi diag(sqrt w) = V Lambda V^* (FP64,
+ * cyclic Jacobi on the GPU), the new atoms are
+ * phi_j = Psi diag(sqrt w) v_j / sqrt(lambda_j) (orthonormal, FP32 combination)
+ * with weights lambda_j / sum(lambda), sorted descending, then P_tau (as in
+ * qst_simplex_project).  In place: psi [K][2^n] complex64 and w [K] float32
+ * (device) receive the K' kept atoms/weights in their first K' slots; the
+ * remaining slots get zero atoms and zero weights (a zero weight removes an
+ * atom from the forward and adjoint).  K_out [1] int (device) receives K'.
+ * The plan's K must be <= 32.
+ */
+qst_status qst_refactor(qst_plan plan, float *psi, float *w, double tau,
+                        int *K_out, void *stream);
+
+/*
+ * One slot of the master loop of Algorithm 1 (Sec. III-C) on the state
+ * (psi [K][2^n] complex64, w [K] float32; device, updated in place when the
+ * proposal is accepted).  Atoms with w_r = 0 are inactive (not part of the
+ * state); R counts the atoms with w_r > 0.
+ *   slot 0 (T_psi): atom r; direction g = w_r (I - psi_r psi_r^*) G psi_r
+ *          (Eq. atom-direction), trial (psi_r + eta g) / ||psi_r + eta g||
+ *          (Eq. atom-trial).
+ *   slot 1 (T_alpha): beta = proj_Delta(w + eta h) over the active atoms with
+ *          h = A^T c (Eqs. h_t, coefficient-update), then P_tau.
+ *   slot 2 (T_rho): the exact spectral refactorisation of rho_t (qst_refactor;
+ *          the spectral step with eta_rho = 0), then P_tau; one proposal.
+ * Step sizes (slots 0, 1): eta = eta0 * eta_ratio^j, j = 0 .. n_eta-1, tried
+ * from largest to smallest; the first proposal with
+ * J(X~) <= J_t - tau_acc (Eq. state-acceptance-rule) is kept, where
+ * J = L_eps + mu R (Eq. fixed-rank-objective).  Defaults (Table I): mu = 1e-3,
+ * tau = 1e-3, tau_acc = 1e-10, grid {2^-j}, j = 0..10.
+ * Host outputs: *J_out (J of the resulting state), *accepted (0/1),
+ * *eta_used.  The call synchronises the stream (it reads each trial's loss).
+ * Data arguments as in qst_forward.
+ */
+typedef struct qst_step_params {
+    double mu, tau, tau_acc, eta0, eta_ratio;
+    int n_eta;
+} qst_step_params;
+void qst_step_params_default(qst_step_params *sp);
+qst_status qst_step(qst_plan plan, int slot, int r, float *psi, float *w,
+                    const uint8_t *basis, const int64_t *row_ptr,
+                    const uint32_t *outcome, const uint32_t *count,
+                    const uint32_t *shots, const qst_step_params *params,
+                    double *J_out, int *accepted, double *eta_used, void *stream);
 
 /*
  * Adjoint without any device allocation.  The paper has no counterpart: this

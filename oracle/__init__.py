@@ -164,3 +164,115 @@ def tangent(psi, w, G_psi):
     G_psi = np.asarray(G_psi, dtype=np.complex128)
     inner = np.sum(np.conj(psi) * G_psi, axis=1)  # <psi_k | G psi_k>
     return np.asarray(w, dtype=np.float64)[:, None] * (G_psi - psi * inner[:, None])
+
+
+# ----------------------------------------------------------------- update-rule helpers (FP64 numpy)
+
+def simplex_project(v):
+    """Euclidean projection of v onto the probability simplex (Eq. coefficient-update's
+    proj_Delta): the sort-based exact method (Held, Wolfe and Crowder 1974; Duchi et al.
+    2008).  Sort descending u, take the largest j with u_j - (sum_{i<=j} u_i - 1)/j > 0,
+    theta = (sum_{i<=j} u_i - 1)/j, beta = max(v - theta, 0)."""
+    v = np.asarray(v, dtype=np.float64)
+    if v.size == 0:
+        return v.copy()
+    u = np.sort(v)[::-1]
+    css = np.cumsum(u)
+    j = np.arange(1, v.size + 1)
+    ok = u - (css - 1.0) / j > 0
+    rho = int(np.nonzero(ok)[0][-1]) + 1
+    theta = (css[rho - 1] - 1.0) / rho
+    return np.maximum(v - theta, 0.0)
+
+
+def prune(beta, tau):
+    """The truncation map P_tau of Sec. III-A (Eq. truncation-map): keep the indices with
+    beta_r > tau (strict), renormalise them to sum 1.  When no index survives, keep the
+    largest one (lowest index on ties).  Returns (kept indices, renormalised weights)."""
+    beta = np.asarray(beta, dtype=np.float64)
+    keep = np.nonzero(beta > tau)[0]
+    if keep.size == 0:
+        keep = np.array([int(np.argmax(beta))])
+    b = beta[keep]
+    return keep, b / b.sum()
+
+
+def refactor(psi, w, tau):
+    """Exact spectral refactorisation of rho = Psi diag(w) Psi^* (the spectral step of
+    Sec. III-C with eta_rho = 0, where its Ritz pairs are exact): through the K x K Gram
+    matrix C = diag(sqrt w) Psi^* Psi diag(sqrt w) = V Lambda V^*, the eigenvectors of rho
+    are phi_j = Psi diag(sqrt w) v_j / sqrt(lambda_j) with eigenvalues lambda_j.  Eigenpairs
+    are sorted descending, weights lambda / sum(lambda), then P_tau.
+    Returns (atoms [K'][D], weights [K'])."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    w = np.asarray(w, dtype=np.float64)
+    sw = np.sqrt(np.maximum(w, 0.0))
+    B = psi.T * sw                     # D x K: columns sqrt(w_k) psi_k
+    C = B.conj().T @ B                 # K x K Hermitian PSD
+    lam, V = np.linalg.eigh(C)
+    order = np.argsort(lam)[::-1]
+    lam, V = lam[order], V[:, order]
+    lam = np.maximum(lam, 0.0)
+    weights = lam / lam.sum()
+    keep, wk = prune(weights, tau)
+    phi = (B @ V[:, keep]) / np.sqrt(lam[keep])
+    return np.ascontiguousarray(phi.T), wk
+
+
+def objective(n, data, psi, w, eps, mu):
+    """J = L_eps(A(Psi) w) + mu R (Eq. fixed-rank-objective), R = number of atoms with
+    w_r > 0 (zero-weight slots are not part of the state)."""
+    f = forward(n, data["basis"], psi, w, data["row_ptr"], data["outcome"], data["count"], data["shots"], eps=eps)
+    R = int(np.count_nonzero(np.asarray(w) > 0))
+    return f["loss"] + mu * R, f
+
+
+def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, eta0=1.0, eta_ratio=0.5,
+         n_eta=11):
+    """One slot of Algorithm 1 with the step grid of Sec. IV (eta = eta0 * eta_ratio^j,
+    j = 0..n_eta-1, largest first; the first accepted proposal is kept) and the
+    acceptance rule J(X~) <= J_t - tau_acc (Eq. state-acceptance-rule).
+      slot 0 (T_psi): atom r, direction g = w_r (I - psi psi^*) G psi_r (Eq. atom-direction),
+             trial psi~ = (psi + eta g)/||psi + eta g|| (Eq. atom-trial).
+      slot 1 (T_alpha): beta = proj_Delta(w + eta h) over the active atoms (Eq.
+             coefficient-update), then P_tau.
+      slot 2 (T_rho): the exact spectral refactorisation of rho_t (eta_rho = 0), then P_tau;
+             one proposal, no step grid.
+    Zero-weight slots are inactive.  Returns (psi, w, J, accepted, eta)."""
+    psi = np.array(psi, dtype=np.complex128)
+    w = np.array(w, dtype=np.float64)
+    J0, f0 = objective(n, data, psi, w, eps, mu)
+    etas = [eta0 * eta_ratio ** j for j in range(n_eta)]
+    if slot == 2:
+        active = np.nonzero(w > 0)[0]
+        phi, wk = refactor(psi[active], w[active], tau)
+        pt = np.zeros_like(psi)
+        wt = np.zeros_like(w)
+        pt[:phi.shape[0]] = phi
+        wt[:wk.size] = wk
+        Jt, _ = objective(n, data, pt, wt, eps, mu)
+        if Jt <= J0 - tau_acc:
+            return pt, wt, Jt, True, 0.0
+        return psi, w, J0, False, 0.0
+    adj = adjoint(n, data["basis"], psi, w, data["row_ptr"], data["outcome"], f0["c_obs"])
+    if slot == 0:
+        g = tangent(psi[r:r + 1], w[r:r + 1], adj["G_psi"][r:r + 1])[0]
+        for eta in etas:
+            t = psi[r] + eta * g
+            pt = psi.copy()
+            pt[r] = t / np.linalg.norm(t)
+            Jt, _ = objective(n, data, pt, w, eps, mu)
+            if Jt <= J0 - tau_acc:
+                return pt, w, Jt, True, eta
+        return psi, w, J0, False, etas[-1]
+    h = adj["h"]
+    active = np.nonzero(w > 0)[0]
+    for eta in etas:
+        beta = simplex_project(w[active] + eta * h[active])
+        keep, b = prune(beta, tau)
+        wt = np.zeros_like(w)
+        wt[active[keep]] = b
+        Jt, _ = objective(n, data, psi, wt, eps, mu)
+        if Jt <= J0 - tau_acc:
+            return psi, wt, Jt, True, eta
+    return psi, w, J0, False, etas[-1]

@@ -957,6 +957,8 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
     }
 }
 
+#include "qst_update.cuh"
+
 // ----------------------------------------------------------------- host side
 
 int ipow3(int r) {
@@ -988,6 +990,17 @@ struct qst_plan_s {
     int loss_parts = 0;
     float2 *zbuf = nullptr;
     double *hdot = nullptr;
+    double2 *refac_C = nullptr;  // K x K Gram (refactorisation)
+    double2 *refac_T = nullptr;  // K x K combination matrix
+    // qst_step workspace
+    float2 *step_trial = nullptr;  // [K][D] trial atoms
+    float2 *step_grad = nullptr;   // [K][D] G psi
+    float *step_c = nullptr;       // [nnz] likelihood ratio of the current state
+    float *step_gw = nullptr;      // [K] weight gradient
+    float *step_tw = nullptr;      // [K] trial weights
+    float *step_m1 = nullptr;      // [K] all -1 (adjoint weights that return G psi)
+    double *step_loss = nullptr;   // [1]
+    int *step_kout = nullptr;      // [1]
     int *status = nullptr;
     int64_t ws_bytes = 0;
     // host-buffer path (allocated on first use)
@@ -1195,6 +1208,21 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc) rc = dalloc(p, &p->loss_part, p->loss_parts);
     if (!rc) rc = dalloc(p, &p->zbuf, (size_t)p->nb_max * K * D);
     if (!rc) rc = dalloc(p, &p->hdot, (size_t)K << c);
+    if (!rc && K <= kRefacMax) rc = dalloc(p, &p->refac_C, (size_t)K * K);
+    if (!rc && K <= kRefacMax) rc = dalloc(p, &p->refac_T, (size_t)K * K);
+    if (!rc) rc = dalloc(p, &p->step_trial, (size_t)K * D);
+    if (!rc) rc = dalloc(p, &p->step_grad, (size_t)K * D);
+    if (!rc) rc = dalloc(p, &p->step_c, nnz);
+    if (!rc) rc = dalloc(p, &p->step_gw, K);
+    if (!rc) rc = dalloc(p, &p->step_tw, K);
+    if (!rc) rc = dalloc(p, &p->step_m1, K);
+    if (!rc) rc = dalloc(p, &p->step_loss, 1);
+    if (!rc) rc = dalloc(p, &p->step_kout, 1);
+    if (!rc) {
+        std::vector<float> m1((size_t)K, -1.0f);
+        if (cudaMemcpy(p->step_m1, m1.data(), sizeof(float) * K, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = QST_ERR_CUDA;
+    }
     if (!rc) rc = dalloc(p, &p->status, 1);
     if (!rc && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) {
@@ -1220,6 +1248,16 @@ qst_status qst_plan_destroy(qst_plan p) {
     cudaFree(p->loss_part);
     cudaFree(p->zbuf);
     cudaFree(p->hdot);
+    cudaFree(p->refac_C);
+    cudaFree(p->refac_T);
+    cudaFree(p->step_trial);
+    cudaFree(p->step_grad);
+    cudaFree(p->step_c);
+    cudaFree(p->step_gw);
+    cudaFree(p->step_tw);
+    cudaFree(p->step_m1);
+    cudaFree(p->step_loss);
+    cudaFree(p->step_kout);
     cudaFree(p->status);
     cudaFree(p->h_dev);
     for (auto &tl : p->pending) {
@@ -1437,6 +1475,159 @@ qst_status qst_plan_launch_count(qst_plan p, int64_t *count) {
     if (!p || !count) return QST_ERR_INVALID_ARG;
     *count = p->total_launches;
     return QST_OK;
+}
+
+qst_status qst_simplex_project(const double *v, int K, double tau, double *beta, int *keep, int *K_out,
+                               void *stream) {
+    if (!v || !beta || !keep || !K_out || K < 1) return QST_ERR_INVALID_ARG;
+    if (K > kProjMax) return QST_ERR_UNSUPPORTED;
+    if (!aligned(v, 8) || !aligned(beta, 8) || !aligned(keep, 4) || !aligned(K_out, 4)) return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_simplex<<<1, kProjMax, 0, st>>>(v, K, tau, beta, keep, K_out);
+    return cudaGetLastError() == cudaSuccess ? QST_OK : QST_ERR_CUDA;
+}
+
+void qst_step_params_default(qst_step_params *sp) {
+    if (!sp) return;
+    sp->mu = 1e-3;
+    sp->tau = 1e-3;
+    sp->tau_acc = 1e-10;
+    sp->eta0 = 1.0;
+    sp->eta_ratio = 0.5;
+    sp->n_eta = 11;
+}
+
+qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uint8_t *basis, const int64_t *row_ptr,
+                    const uint32_t *outcome, const uint32_t *count, const uint32_t *shots,
+                    const qst_step_params *params, double *J_out, int *accepted, double *eta_used, void *stream) {
+    if (!p || !psi || !w || !basis || !row_ptr || !shots || !J_out || !accepted || !eta_used) return QST_ERR_INVALID_ARG;
+    if (slot < 0 || slot > 2 || (slot == 0 && (r < 0 || r >= p->K))) return QST_ERR_INVALID_ARG;
+    if (p->K > kProjMax || (slot == 2 && !p->refac_C)) return QST_ERR_UNSUPPORTED;
+    qst_step_params sp;
+    qst_step_params_default(&sp);
+    if (params) sp = *params;
+    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0)) return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = p->K;
+    const size_t D = (size_t)1 << p->n;
+    std::vector<float> wh((size_t)K);
+    // J = L_eps + mu R for the state (ps, ww); R counts the atoms with w > 0.
+    auto evaluate = [&](const float *ps, const float *ww, float *c_out, double *J) -> qst_status {
+        qst_status rc = qst_forward(p, ps, ww, basis, row_ptr, outcome, count, shots, nullptr, c_out, p->step_loss,
+                                    nullptr, stream);
+        if (rc) return rc;
+        double L = 0.0;
+        if (cudaMemcpyAsync(&L, p->step_loss, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(wh.data(), ww, sizeof(float) * K, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return QST_ERR_CUDA;
+        int R = 0;
+        for (int k = 0; k < K; ++k) R += wh[k] > 0.f;
+        *J = L + sp.mu * R;
+        return QST_OK;
+    };
+    double J0 = 0.0;
+    qst_status rc = evaluate(psi, w, p->step_c, &J0);
+    if (rc) return rc;
+    *J_out = J0;
+    *accepted = 0;
+    *eta_used = 0.0;
+    float *trial_psi = reinterpret_cast<float *>(p->step_trial);
+    if (slot == 2) {  // exact spectral refactorisation (eta_rho = 0)
+        if (cudaMemcpyAsync(trial_psi, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(p->step_tw, w, sizeof(float) * K, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return QST_ERR_CUDA;
+        rc = qst_refactor(p, trial_psi, p->step_tw, sp.tau, p->step_kout, stream);
+        if (rc) return rc;
+        double Jt = 0.0;
+        rc = evaluate(trial_psi, p->step_tw, nullptr, &Jt);
+        if (rc) return rc;
+        if (Jt <= J0 - sp.tau_acc) {
+            if (cudaMemcpyAsync(psi, trial_psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(w, p->step_tw, sizeof(float) * K, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return QST_ERR_CUDA;
+            *J_out = Jt;
+            *accepted = 1;
+        }
+        return QST_OK;
+    }
+    double eta = sp.eta0;
+    if (slot == 0) {  // atom r (Eqs. atom-direction, atom-trial)
+        rc = qst_adjoint(p, psi, p->step_m1, basis, row_ptr, outcome, p->step_c,
+                         reinterpret_cast<float *>(p->step_grad), nullptr, stream);
+        if (rc) return rc;
+        if (cudaMemcpyAsync(trial_psi, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return QST_ERR_CUDA;
+        const float2 *psr = reinterpret_cast<const float2 *>(psi) + (size_t)r * D;
+        float2 *out = p->step_trial + (size_t)r * D;
+        for (int j = 0; j < sp.n_eta; ++j, eta *= sp.eta_ratio) {
+            rc = launch(p, QST_KERNEL_STEP, st, [&] {
+                k_atom_trial<<<1, 1024, 0, st>>>(psr, p->step_grad + (size_t)r * D, wh[r], eta, (int64_t)D, out);
+            });
+            if (rc) return rc;
+            double Jt = 0.0;
+            rc = evaluate(trial_psi, w, nullptr, &Jt);
+            if (rc) return rc;
+            if (Jt <= J0 - sp.tau_acc) {
+                if (cudaMemcpyAsync(reinterpret_cast<float2 *>(psi) + (size_t)r * D, out, sizeof(float2) * D,
+                                    cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return QST_ERR_CUDA;
+                *J_out = Jt;
+                *accepted = 1;
+                *eta_used = eta;
+                return QST_OK;
+            }
+        }
+        *eta_used = eta / sp.eta_ratio;
+        return QST_OK;
+    }
+    // slot 1: coefficients (Eq. coefficient-update, then P_tau)
+    rc = qst_adjoint(p, psi, w, basis, row_ptr, outcome, p->step_c, reinterpret_cast<float *>(p->step_grad),
+                     p->step_gw, stream);
+    if (rc) return rc;
+    for (int j = 0; j < sp.n_eta; ++j, eta *= sp.eta_ratio) {
+        rc = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_coeff_trial<<<1, kProjMax, 0, st>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw);
+        });
+        if (rc) return rc;
+        double Jt = 0.0;
+        rc = evaluate(psi, p->step_tw, nullptr, &Jt);
+        if (rc) return rc;
+        if (Jt <= J0 - sp.tau_acc) {
+            if (cudaMemcpyAsync(w, p->step_tw, sizeof(float) * K, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return QST_ERR_CUDA;
+            *J_out = Jt;
+            *accepted = 1;
+            *eta_used = eta;
+            return QST_OK;
+        }
+    }
+    *eta_used = eta / sp.eta_ratio;
+    return QST_OK;
+}
+
+qst_status qst_refactor(qst_plan p, float *psi, float *w, double tau, int *K_out, void *stream) {
+    if (!p || !psi || !w || !K_out) return QST_ERR_INVALID_ARG;
+    if (p->K > kRefacMax || !p->refac_C) return QST_ERR_UNSUPPORTED;
+    if (!aligned(psi, 16) || !aligned(w, 4) || !aligned(K_out, 4)) return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = p->K;
+    const int64_t D = (int64_t)1 << p->n;
+    float2 *ps = reinterpret_cast<float2 *>(psi);
+    qst_status rc = launch(p, QST_KERNEL_REFACTOR, st, [&] {
+        k_gram<<<K * (K + 1) / 2, 256, 0, st>>>(ps, K, D, p->refac_C);
+    });
+    if (rc) return rc;
+    rc = launch(p, QST_KERNEL_REFACTOR, st, [&] {
+        k_eig<<<1, kRefacMax, 0, st>>>(p->refac_C, w, K, tau, p->refac_T, w, K_out);
+    });
+    if (rc) return rc;
+    const int64_t blocks = (D + 255) / 256;
+    const int grid = (int)(blocks < 148 * 8 ? blocks : 148 * 8);
+    return launch(p, QST_KERNEL_REFACTOR, st, [&] { k_combine<<<grid, 256, 0, st>>>(ps, K, D, p->refac_T); });
 }
 
 }  // extern "C"

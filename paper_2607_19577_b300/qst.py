@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "unsupported size", 3: "CUDA 
                 4: "out of device memory", 5: "device-side error"}
 DEV_BITS = {1: "bad basis code", 2: "malformed CSR counts", 4: "zero shots on a non-empty row",
             8: "non-finite loss"}
-KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue"]
+KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue", "refactor"]
 
 
 class QSTError(RuntimeError):
@@ -38,6 +38,11 @@ class _Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm_settings", ctypes.c_int),
                 ("chunk_qubits", ctypes.c_int), ("max_bin_settings", ctypes.c_int),
                 ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int)]
+
+
+class _StepParams(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("tau", ctypes.c_double), ("tau_acc", ctypes.c_double),
+                ("eta0", ctypes.c_double), ("eta_ratio", ctypes.c_double), ("n_eta", ctypes.c_int)]
 
 
 _lib = None
@@ -67,10 +72,16 @@ def load():
         lib.qst_plan_reset_stats.argtypes = [P]
         lib.qst_plan_launch_count.argtypes = [P, ctypes.POINTER(i64)]
         lib.qst_adjoint_noalloc.argtypes = [i32, i32, i32, i64, ctypes.POINTER(_Params)] + [P] * 9 + [P]
+        lib.qst_simplex_project.argtypes = [P, i32, f64, P, P, P, P]
+        lib.qst_refactor.argtypes = [P, P, P, f64, P, P]
+        lib.qst_step_params_default.argtypes = [ctypes.POINTER(_StepParams)]
+        lib.qst_step_params_default.restype = None
+        lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
+                                 ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
         for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_forward",
                      "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
-                     "qst_adjoint_noalloc"]:
+                     "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step"]:
             getattr(lib, name).restype = i32
         _lib = lib
     return _lib
@@ -220,6 +231,32 @@ class Plan:
         _check(rc, "qst_evaluate_host")
         return float(loss[0]), gp, gw
 
+    def refactor(self, psi, w, tau, k_out=None):
+        """qst_refactor, in place on psi [K][D] complex64 and w [K] float32; returns
+        the device int tensor holding the number of kept atoms."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(w, torch.float32, (self.K,), "w")
+        k_out = torch.zeros(1, dtype=torch.int32, device=psi.device) if k_out is None else k_out
+        _check(load().qst_refactor(self._h, _ptr(psi), _ptr(w), float(tau), _ptr(k_out), _stream()),
+               "qst_refactor")
+        return k_out
+
+    def step(self, slot, r, psi, w, d: Data, **params):
+        """qst_step: one slot of Algorithm 1 (0 = atom r, 1 = coefficients, 2 = refactor),
+        in place on psi and w.  Returns (J, accepted, eta_used)."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(w, torch.float32, (self.K,), "w")
+        self._data(d)
+        sp = _StepParams()
+        load().qst_step_params_default(ctypes.byref(sp))
+        for k, v in params.items():
+            setattr(sp, k, v)
+        J, acc, eta = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+        _check(load().qst_step(self._h, int(slot), int(r), _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr),
+                               _ptr(d.outcome), _ptr(d.count), _ptr(d.shots), ctypes.byref(sp), ctypes.byref(J),
+                               ctypes.byref(acc), ctypes.byref(eta), _stream()), "qst_step")
+        return J.value, bool(acc.value), eta.value
+
     def status(self):
         """Synchronise and return the device status bits (0 = clean)."""
         st = ctypes.c_int()
@@ -273,6 +310,19 @@ class QSTLoss(torch.autograd.Function):
         grad_psi, grad_w = ctx.plan.adjoint(psi, w, ctx.data, c_obs)
         g32 = g.to(torch.float32)
         return 2.0 * g32 * grad_psi, g32 * grad_w, None, None
+
+
+def simplex_project(v, tau, beta=None, keep=None, k_out=None):
+    """qst_simplex_project: v float64 [K] CUDA tensor -> (beta [K], keep [K] int32, k_out [1] int32)."""
+    if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64 and v.dim() == 1):
+        raise QSTError("v must be a 1-D float64 CUDA tensor")
+    K = v.shape[0]
+    beta = torch.empty_like(v) if beta is None else beta
+    keep = torch.empty(K, dtype=torch.int32, device=v.device) if keep is None else keep
+    k_out = torch.empty(1, dtype=torch.int32, device=v.device) if k_out is None else k_out
+    _check(load().qst_simplex_project(_ptr(v.contiguous()), int(K), float(tau), _ptr(beta), _ptr(keep),
+                                      _ptr(k_out), _stream()), "qst_simplex_project")
+    return beta, keep, k_out
 
 
 QST_ERR_SCRATCH_TOO_SMALL = 6

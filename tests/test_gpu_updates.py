@@ -1,0 +1,120 @@
+"""GPU simplex projection (+ P_tau) and spectral refactorisation against the
+FP64 oracle.  The refactor is compared through rho-level quantities (atoms
+carry a free phase and degenerate eigenvalues a free basis): weights, the
+Frobenius distance between the old and new rho computed from Gram matrices,
+and orthonormality of the new atoms."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_19577_b300 import qst, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("K,seed,tau", [(1, 0, 1e-3), (2, 1, 1e-3), (7, 2, 0.0), (16, 3, 1e-3), (100, 4, 1e-3),
+                                        (1024, 5, 1e-4), (33, 6, 0.05)])
+def test_simplex_project_matches_oracle(K, seed, tau):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(K) * 0.3 + 1.0 / K
+    beta, keep, kout = qst.simplex_project(torch.from_numpy(v).cuda(), tau)
+    torch.cuda.synchronize()
+    ref = oracle.simplex_project(v)
+    rkeep, rb = oracle.prune(ref, tau)
+    k = int(kout.item())
+    assert k == rkeep.size
+    assert list(keep.cpu().numpy()[:k]) == list(rkeep)
+    full = np.zeros(K)
+    full[rkeep] = rb
+    np.testing.assert_allclose(beta.cpu().numpy(), full, atol=1e-14)
+
+
+def test_simplex_project_ties_and_nothing_survives():
+    v = np.array([0.25, 0.25, 0.25, 0.25])
+    beta, keep, kout = qst.simplex_project(torch.from_numpy(v).cuda(), 0.3)  # all equal, none > 0.3
+    assert int(kout.item()) == 1 and int(keep[0].item()) == 0
+    np.testing.assert_allclose(beta.cpu().numpy(), [1, 0, 0, 0])
+
+
+def _gram_frob2(A, wa, B, wb):
+    """||A^T diag(wa) A^* - B^T diag(wb) B^*||_F^2 through K x K Gram matrices."""
+    def cross(X, wx, Y, wy):
+        G = X.conj() @ Y.T
+        return float(np.real(np.sum(np.outer(wx, wy) * np.abs(G) ** 2)))
+    return cross(A, wa, A, wa) + cross(B, wb, B, wb) - 2 * cross(A, wa, B, wb)
+
+
+@pytest.mark.parametrize("n,K,seed", [(4, 3, 0), (8, 8, 1), (12, 16, 2), (16, 16, 3), (10, 32, 4)])
+def test_refactor_matches_oracle(n, K, seed):
+    rng = synth.rng_for(seed, 55)
+    psi = synth.random_atoms(n, K, rng).astype(np.complex64)
+    w = synth.dirichlet_weights(K, rng)
+    w[-1] = 2e-4  # below tau after renormalisation: gets pruned
+    w = (w / w.sum()).astype(np.float32)
+    tau = 1e-3
+    plan = qst.Plan(n, 4, K, 0)
+    tp, tw = torch.from_numpy(psi.copy()).cuda(), torch.from_numpy(w.copy()).cuda()
+    kout = plan.refactor(tp, tw, tau)
+    torch.cuda.synchronize()
+    k = int(kout.item())
+    phi, wk = oracle.refactor(psi.astype(np.complex128), w.astype(np.float64), tau)
+    assert k == phi.shape[0]
+    gp = tp.cpu().numpy().astype(np.complex128)
+    gw = tw.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(gw[:k], wk, rtol=1e-5, atol=1e-7)
+    assert np.all(gw[k:] == 0) and np.all(gp[k:] == 0)
+    np.testing.assert_allclose(gp[:k].conj() @ gp[:k].T, np.eye(k), atol=2e-5)
+    # rho' against the oracle's rho' (same pruning) and, before pruning effects, against rho
+    d2 = _gram_frob2(gp[:k], gw[:k], phi, wk)
+    assert d2 <= 1e-9, d2
+    plan.close()
+
+
+def test_refactor_of_orthonormal_atoms_is_identity_on_rho():
+    n, K = 9, 5
+    a = synth.random_atoms(n, K, synth.rng_for(9), orthonormal=True).astype(np.complex64)
+    w = np.array([0.4, 0.25, 0.2, 0.1, 0.05], np.float32)
+    plan = qst.Plan(n, 4, K, 0)
+    tp, tw = torch.from_numpy(a.copy()).cuda(), torch.from_numpy(w.copy()).cuda()
+    plan.refactor(tp, tw, 0.0)
+    gp, gw = tp.cpu().numpy().astype(np.complex128), tw.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(gw, w, atol=1e-6)
+    assert _gram_frob2(gp, gw, a.astype(np.complex128), w.astype(np.float64)) <= 1e-10
+    plan.close()
+
+
+def test_step_sequence_matches_oracle():
+    """A sequence of Algorithm-1 slots (atom, coefficient and refactor slots) on the
+    GPU and in the oracle: same acceptance decisions and step sizes, J within 1e-5,
+    and the same state at the rho level; J never increases."""
+    inst = synth.make_instance("n4_all81", seed=7, K=4)
+    n = inst.n
+    psi0 = inst.psi.astype(np.complex128)
+    psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
+    w0 = inst.w.astype(np.float64)
+    data = dict(basis=inst.basis, row_ptr=inst.row_ptr, outcome=inst.outcome, count=inst.count, shots=inst.shots)
+    plan = qst.Plan(n, inst.M, inst.K, inst.nnz)
+    d = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    tp = torch.from_numpy(psi0.astype(np.complex64)).cuda()
+    tw = torch.from_numpy(w0.astype(np.float32)).cuda()
+    op = tp.cpu().numpy().astype(np.complex128)
+    ow = tw.cpu().numpy().astype(np.float64)
+    J_prev = None
+    for slot, r in [(0, 0), (1, 0), (0, 1), (0, 2), (0, 3), (1, 0), (2, 0), (0, 0), (1, 0), (0, 1)]:
+        J, acc, eta = plan.step(slot, r, tp, tw, d)
+        op, ow, oJ, oacc, oeta = oracle.step(n, data, op, ow, slot, r)
+        assert acc == oacc and abs(eta - oeta) <= 1e-12 * max(1.0, oeta), (slot, r, acc, oacc, eta, oeta)
+        assert abs(J - oJ) <= 1e-5 * abs(oJ), (J, oJ)
+        gp = tp.cpu().numpy().astype(np.complex128)
+        gw = tw.cpu().numpy().astype(np.float64)
+        a = gw > 0
+        b = ow > 0
+        d2 = _gram_frob2(gp[a], gw[a], op[b], ow[b])
+        assert d2 <= 1e-9, (slot, d2)
+        if J_prev is not None:
+            assert J <= J_prev + 1e-12
+        J_prev = J
+        # continue the oracle from the GPU state (FP32), so differences do not accumulate
+        op, ow = gp, gw
+    plan.close()
