@@ -225,6 +225,33 @@ qst_status qst_step(qst_plan plan, int slot, int r, float *psi, float *w,
                     double *J_out, int *accepted, double *eta_used, void *stream);
 
 /*
+ * Batched evaluation of many independent instances of uneven shape (the
+ * batched workload of the benchmark spec: instances with different n, M, K and
+ * shots).  qst_batch_create makes one plan per instance (params shared).
+ * qst_batch_evaluate runs every instance's qst_forward + qst_adjoint; arguments
+ * are HOST arrays of `count` DEVICE pointers, one per instance, with the
+ * per-instance layouts of qst_forward / qst_adjoint (loss[i] -> double[1],
+ * c_obs[i] -> float[nnz_i], grad_psi[i] -> complex64[K_i][2^n_i],
+ * grad_w[i] -> float[K_i]).  The first call with a given set of pointers
+ * captures all instances into one CUDA graph, with each instance on its own
+ * forked stream so they run concurrently; later calls with the same pointers
+ * replay it as a single graph launch on `stream` (the graph is captured on a
+ * batch-owned stream in thread-local mode).
+ * qst_batch_plan returns instance i's plan (for qst_plan_status etc.).
+ */
+typedef struct qst_batch_s *qst_batch;
+qst_status qst_batch_create(qst_batch *batch, int count, const int *n, const int *M,
+                            const int *K, const int64_t *nnz, const qst_params *params);
+qst_status qst_batch_destroy(qst_batch batch);
+qst_status qst_batch_plan(qst_batch batch, int i, qst_plan *plan);
+qst_status qst_batch_evaluate(qst_batch batch, const float *const *psi, const float *const *w,
+                              const uint8_t *const *basis, const int64_t *const *row_ptr,
+                              const uint32_t *const *outcome, const uint32_t *const *count,
+                              const uint32_t *const *shots, double *const *loss,
+                              float *const *c_obs, float *const *grad_psi,
+                              float *const *grad_w, void *stream);
+
+/*
  * Adjoint without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc.  Examples are
  * code running under an allocator it does not own (a framework's caching

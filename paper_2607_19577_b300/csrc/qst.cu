@@ -1745,3 +1745,140 @@ extern "C" qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz, cons
     // tmp owns nothing: its workspace pointers are views of the scratch array
     return qst_adjoint(&tmp, psi, w, basis, row_ptr, outcome, c_obs, grad_psi, grad_w, stream);
 }
+
+// ----------------------------------------------------------------- batched instances
+//
+// Many independent instances of uneven shape (n, M, K, nnz): one plan per
+// instance, and one CUDA graph per set of buffers.  The graph forks every
+// instance's forward + adjoint onto its own stream, so the instances run
+// concurrently and the whole batch is one graph launch.
+
+struct qst_batch_s {
+    int count = 0;
+    std::vector<qst_plan> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> fork, join;
+    cudaEvent_t start = nullptr;
+    cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy default stream)
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> key;  // buffers the graph was captured with
+};
+
+namespace {
+constexpr int kBatchStreams = 16;
+}
+
+extern "C" qst_status qst_batch_destroy(qst_batch b) {
+    if (!b) return QST_ERR_INVALID_ARG;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto p : b->plans)
+        if (p) qst_plan_destroy(p);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto e : b->fork) cudaEventDestroy(e);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->start) cudaEventDestroy(b->start);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return QST_OK;
+}
+
+extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, const int *M, const int *K,
+                                       const int64_t *nnz, const qst_params *params) {
+    if (!out || count < 1 || !n || !M || !K || !nnz) return QST_ERR_INVALID_ARG;
+    *out = nullptr;
+    qst_batch b = new (std::nothrow) qst_batch_s;
+    if (!b) return QST_ERR_NO_MEMORY;
+    b->count = count;
+    b->plans.assign(count, nullptr);
+    for (int i = 0; i < count; ++i) {
+        const qst_status rc = qst_plan_create(&b->plans[i], n[i], M[i], K[i], nnz[i], params);
+        if (rc) {
+            qst_batch_destroy(b);
+            return rc;
+        }
+    }
+    const int ns = count < kBatchStreams ? count : kBatchStreams;
+    b->streams.assign(ns, nullptr);
+    b->fork.assign(ns, nullptr);
+    b->join.assign(ns, nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int j = 0; j < ns && ok; ++j)
+        ok = cudaStreamCreateWithFlags(&b->streams[j], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->fork[j], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        qst_batch_destroy(b);
+        return QST_ERR_CUDA;
+    }
+    *out = b;
+    return QST_OK;
+}
+
+extern "C" qst_status qst_batch_plan(qst_batch b, int i, qst_plan *plan) {
+    if (!b || !plan || i < 0 || i >= b->count) return QST_ERR_INVALID_ARG;
+    *plan = b->plans[i];
+    return QST_OK;
+}
+
+extern "C" qst_status qst_batch_evaluate(qst_batch b, const float *const *psi, const float *const *w,
+                                         const uint8_t *const *basis, const int64_t *const *row_ptr,
+                                         const uint32_t *const *outcome, const uint32_t *const *count,
+                                         const uint32_t *const *shots, double *const *loss, float *const *c_obs,
+                                         float *const *grad_psi, float *const *grad_w, void *stream) {
+    if (!b || !psi || !w || !basis || !row_ptr || !outcome || !count || !shots || !loss || !c_obs || !grad_psi ||
+        !grad_w)
+        return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<const void *> key;
+    key.reserve((size_t)b->count * 11);
+    for (int i = 0; i < b->count; ++i) {
+        const void *ptrs[11] = {psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i],
+                                loss[i], c_obs[i], grad_psi[i], grad_w[i]};
+        for (const void *q : ptrs) key.push_back(q);
+        if (!psi[i] || !w[i] || !basis[i] || !row_ptr[i] || !shots[i] || !loss[i] || !grad_psi[i] || !grad_w[i])
+            return QST_ERR_INVALID_ARG;
+    }
+    if (!b->exec || key != b->key) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cs = b->cap;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return QST_ERR_CUDA;
+        }
+        qst_status rc = QST_OK;
+        const int ns = (int)b->streams.size();
+        if (cudaEventRecord(b->start, cs) != cudaSuccess) rc = QST_ERR_CUDA;
+        for (int j = 0; j < ns && !rc; ++j)
+            if (cudaStreamWaitEvent(b->streams[j], b->start, 0) != cudaSuccess) rc = QST_ERR_CUDA;
+        for (int i = 0; i < b->count && !rc; ++i) {
+            void *si = (void *)b->streams[i % ns];
+            rc = qst_forward(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i], nullptr,
+                             c_obs[i], loss[i], nullptr, si);
+            if (!rc)
+                rc = qst_adjoint(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], c_obs[i], grad_psi[i],
+                                 grad_w[i], si);
+        }
+        for (int j = 0; j < ns && !rc; ++j)
+            if (cudaEventRecord(b->join[j], b->streams[j]) != cudaSuccess || cudaStreamWaitEvent(cs, b->join[j], 0) != cudaSuccess)
+                rc = QST_ERR_CUDA;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        if (rc || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc ? rc : QST_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            b->exec = nullptr;
+            return QST_ERR_CUDA;
+        }
+        b->key = key;
+    }
+    return cudaGraphLaunch(b->exec, st) == cudaSuccess ? QST_OK : QST_ERR_CUDA;
+}

@@ -74,6 +74,10 @@ def load():
         lib.qst_adjoint_noalloc.argtypes = [i32, i32, i32, i64, ctypes.POINTER(_Params)] + [P] * 9 + [P]
         lib.qst_simplex_project.argtypes = [P, i32, f64, P, P, P, P]
         lib.qst_refactor.argtypes = [P, P, P, f64, P, P]
+        lib.qst_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, P, ctypes.POINTER(_Params)]
+        lib.qst_batch_destroy.argtypes = [P]
+        lib.qst_batch_plan.argtypes = [P, i32, ctypes.POINTER(P)]
+        lib.qst_batch_evaluate.argtypes = [P] + [P] * 11 + [P]
         lib.qst_step_params_default.argtypes = [ctypes.POINTER(_StepParams)]
         lib.qst_step_params_default.restype = None
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
@@ -81,7 +85,8 @@ def load():
         for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_forward",
                      "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
-                     "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step"]:
+                     "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
+                     "qst_batch_create", "qst_batch_destroy", "qst_batch_plan", "qst_batch_evaluate"]:
             getattr(lib, name).restype = i32
         _lib = lib
     return _lib
@@ -348,6 +353,48 @@ def adjoint_noalloc(psi, w, d: Data, c_obs, grad_psi, grad_w, device_status, par
                                       ctypes.byref(prm) if prm is not None else None,
                                       _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr), _ptr(d.outcome),
                                       _ptr(c_obs), _ptr(grad_psi), _ptr(grad_w), _ptr(device_status), _stream())
+
+
+class Batch:
+    """qst_batch: many independent instances evaluated as one captured CUDA graph."""
+
+    def __init__(self, shapes, eps=1e-8, **plan_kw):
+        """shapes: list of (n, M, K, nnz)."""
+        lib = load()
+        prm = _Params()
+        lib.qst_params_default(ctypes.byref(prm))
+        prm.eps = float(eps)
+        for k, v in plan_kw.items():
+            setattr(prm, k, v)
+        arr = lambda vals, ct: (ct * len(vals))(*vals)  # noqa: E731
+        self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        h = ctypes.c_void_p()
+        _check(lib.qst_batch_create(ctypes.byref(h), len(shapes), arr([s[0] for s in shapes], ctypes.c_int),
+                                    arr([s[1] for s in shapes], ctypes.c_int), arr([s[2] for s in shapes], ctypes.c_int),
+                                    arr([s[3] for s in shapes], ctypes.c_int64), ctypes.byref(prm)), "qst_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().qst_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def evaluate(self, psis, ws, datas, losses, c_obss, grads, grad_ws):
+        """All arguments are lists (one entry per instance) of CUDA tensors."""
+        cnt = len(self.shapes)
+        P = ctypes.c_void_p * cnt
+        ptrs = lambda ts: P(*[t.data_ptr() for t in ts])  # noqa: E731
+        _check(load().qst_batch_evaluate(self._h, ptrs(psis), ptrs(ws), ptrs([d.basis for d in datas]),
+                                         ptrs([d.row_ptr for d in datas]), ptrs([d.outcome for d in datas]),
+                                         ptrs([d.count for d in datas]), ptrs([d.shots for d in datas]),
+                                         ptrs(losses), ptrs(c_obss), ptrs(grads), ptrs(grad_ws), _stream()),
+               "qst_batch_evaluate")
 
 
 def qst_loss(psi, w, plan: Plan, data: Data):

@@ -214,3 +214,30 @@ def random_instance(n: int, M: int, K: int, shots: int, seed: int, dense_frac: f
     w = dirichlet_weights(K, rng_for(seed, 10)).astype(np.float32) if K > 0 else np.zeros(0, np.float32)
     return Instance(name="random", n=n, basis=basis, shots=shots_arr, row_ptr=row_ptr,
                     outcome=outcome, count=count, psi=psi, w=w)
+
+
+def make_batch(seed: int = 0, count: int = 64, n_range=(6, 14), M_range=(200, 3000), shots_range=(500, 5000),
+               rank_range=(1, 8), probs_fn=None):
+    """The batched workload: `count` independent instances with n uniform in n_range,
+    truth rank uniform in rank_range, M uniform in M_range random Pauli strings,
+    shots uniform in shots_range, K = 2 x rank atoms; instance i draws from stream i
+    of the seed."""
+    out = []
+    for i in range(count):
+        rng = rng_for(seed, 10_000 + i)
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        rank = int(rng.integers(rank_range[0], rank_range[1] + 1))
+        M = int(rng.integers(M_range[0], M_range[1] + 1))
+        shots = int(rng.integers(shots_range[0], shots_range[1] + 1))
+        basis = pauli_settings(n, M, rng)
+        tw, ta = dirichlet_weights(rank, rng), random_atoms(n, rank, rng)
+        shots_arr = np.full(M, shots, dtype=np.uint32)
+        if probs_fn is not None:
+            row_ptr, outcome, count_ = counts_from_probs(probs_fn(basis, tw, ta), shots_arr, rng_for(seed, 20_000 + i))
+        else:
+            row_ptr, outcome, count_ = surrogate_counts(n, shots_arr, tw, rng_for(seed, 20_000 + i))
+        psi, w = eval_point(ta, 2 * rank, rng_for(seed, 30_000 + i))
+        out.append(Instance(name=f"batch{i}", n=n, basis=basis, shots=shots_arr, row_ptr=row_ptr, outcome=outcome,
+                            count=count_, psi=psi.astype(np.complex64), w=w.astype(np.float32),
+                            truth_w=tw, truth_atoms=ta))
+    return out
