@@ -71,7 +71,9 @@ void qst_params_default(qst_params *p);
 const char *qst_status_string(qst_status s);
 
 /*
- * Create a plan for one problem shape: n qubits (1 <= n <= 16 in this build),
+ * Create a plan for one problem shape: n qubits (1 <= n <= 20 in this build;
+ * n <= 16 bins settings by their high-bit pattern, n = 17..20 applies the 8
+ * high-bit factors by butterfly passes per setting group),
  * M >= 1 settings, K >= 1 atoms, nnz >= 0 observed (setting, outcome) pairs.
  * Allocates the device workspace (owned by the plan, freed by
  * qst_plan_destroy) on the current CUDA device.  params may be NULL.
@@ -151,7 +153,8 @@ enum {
     QST_KERNEL_EPILOGUE = 7,
     QST_KERNEL_REFACTOR = 8,
     QST_KERNEL_STEP = 9,
-    QST_KERNEL_KINDS = 10
+    QST_KERNEL_HIGH = 10,
+    QST_KERNEL_KINDS = 11
 };
 qst_status qst_plan_set_timing(qst_plan plan, int enable);
 qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,

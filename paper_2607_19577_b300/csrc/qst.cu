@@ -641,6 +641,7 @@ struct FwdArgs {
     float *ppart;      // [K][nnz]: w_k |(V_s psi_k)_u|^2 at observed outcomes
     float *p_dense;    // optional [M][D] (accumulated with atomics; zeroed by the host)
     int64_t nnz;
+    int64_t src_bin_stride;  // elements between the sources of consecutive bins (0: all bins read psi)
     int n, r, K;
 };
 
@@ -686,7 +687,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
     const float wk = a.w[k];
     float *pk = a.ppart + (size_t)k * a.nnz;
     issue(0);
-    build_source<C, RA>(src, a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
+    build_source<C, RA>(src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)k * D, f, b.xytop, b.ytop, tid);
     if (bcount > 0) build_lut<G::TB>(plans_sm[0], lut, tid, G::T);
     __syncthreads();
     for (int si = 0; si < bcount; ++si) {
@@ -767,6 +768,7 @@ struct AdjArgs {
     const float *c_obs;
     const int32_t *choff;
     float2 *zbuf;    // [bins][K][D]
+    int64_t src_bin_stride;  // elements between the sources of consecutive bins (0: all bins read psi)
     int n, r, K;
 };
 
@@ -833,7 +835,8 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
         }
     };
     issue(0);
-    build_source<C, RA>(const_cast<float2 *>(src), a.psi + (size_t)k * D, f, b.xytop, b.ytop, tid);
+    build_source<C, RA>(const_cast<float2 *>(src), a.psi + (size_t)bin * a.src_bin_stride + (size_t)k * D, f, b.xytop,
+                        b.ytop, tid);
     if (bcount > 0) build_lut<G::TB>(plans_sm[0], lut, tid, G::T);
     cp_async_wait0();
     __syncthreads();  // c buffer zeroed, source built, round tables ready
@@ -958,6 +961,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 }
 
 #include "qst_update.cuh"
+#include "qst_wide.cuh"
 
 // ----------------------------------------------------------------- host side
 
@@ -976,6 +980,10 @@ struct TimedLaunch {
 
 struct qst_plan_s {
     int n = 0, M = 0, K = 0, c = 0, r = 0, A = 0, T = 0, smax = 0, nb_max = 0, B = 0;
+    bool wide = false;       // n = 17..20: high bits by butterfly passes, groups of wide_G settings
+    int wide_G = 0;
+    float2 *wide_T = nullptr;    // [wide_G][K][D] intermediate (also the z buffer)
+    double2 *wide_acc = nullptr; // [K][D] FP64 accumulator of G psi
     int64_t nnz = 0;
     qst_params prm{};
     int device = 0;
@@ -1113,8 +1121,9 @@ void with_geo(int c, int ra, Fn &&fn) {
 qst_status prepare(qst_plan p, const uint8_t *basis, const int64_t *row_ptr, const uint32_t *outcome,
                    const uint32_t *shots, cudaStream_t st) {
     qst_status rc = launch(p, QST_KERNEL_PACK, st, [&] {
-        k_pack<<<1, 1024, 0, st>>>(basis, p->M, p->n, p->c, p->r, p->smax, p->A, p->plans, p->order,
-                                   p->bins, p->n_bins, p->status);
+        // the wide path does not bin by the high pattern: one key, one bin
+        k_pack<<<1, 1024, 0, st>>>(basis, p->M, p->n, p->c, p->wide ? 0 : p->r, p->wide ? p->M : p->smax, p->A,
+                                   p->plans, p->order, p->bins, p->n_bins, p->status);
     });
     if (rc) return rc;
     const int warps_per_block = 8;
@@ -1122,6 +1131,102 @@ qst_status prepare(qst_plan p, const uint8_t *basis, const int64_t *row_ptr, con
     return launch(p, QST_KERNEL_VALIDATE, st, [&] {
         k_validate<<<grid, 32 * warps_per_block, 0, st>>>(row_ptr, outcome, shots, p->M, p->nnz, p->n, p->c,
                                                           p->r, p->prm.validate, p->choff, p->status);
+    });
+}
+
+}  // namespace
+
+namespace {
+
+// Wide path, forward: per atom and group of settings, the high pass into the
+// intermediate, then the chunk kernel on single-setting bins reading it.
+qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int64_t *row_ptr,
+                        const uint32_t *outcome, float *p_dense, cudaStream_t st) {
+    const size_t D = (size_t)1 << p->n;
+    const int tiles = (1 << p->c) / kWideCols;
+    for (int g0 = 0; g0 < p->M; g0 += p->wide_G) {
+        const int G = (p->M - g0) < p->wide_G ? (p->M - g0) : p->wide_G;
+        qst_status rc = launch(p, QST_KERNEL_HIGH, st, [&] {
+            k_high_fwd<<<dim3(tiles, G, p->K), 256, 0, st>>>(psi, p->plans, g0, p->K, p->c, p->wide_T);
+        });
+        if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] { k_wide_bins<<<1, 256, 0, st>>>(g0, G, p->bins, p->n_bins); });
+        if (rc) return rc;
+        FwdArgs a;
+        a.psi = p->wide_T;
+        a.w = w;
+        a.plans = p->plans;
+        a.order = p->order;
+        a.bins = p->bins;
+        a.n_bins = p->n_bins;
+        a.row_ptr = row_ptr;
+        a.outcome = outcome;
+        a.choff = p->choff;
+        a.ppart = p->ppart;
+        a.p_dense = p_dense;
+        a.nnz = p->nnz;
+        a.src_bin_stride = (int64_t)p->K * (int64_t)D;
+        a.n = p->n;
+        a.r = p->r;
+        a.K = p->K;
+        const int grid = (G << p->r) * p->K;
+        rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
+            with_geo(p->c, p->A, [&](auto cc, auto ra) {
+                constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+                k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
+            });
+        });
+        if (rc) return rc;
+    }
+    return QST_OK;
+}
+
+// Wide path, adjoint: per atom and group, high pass, chunk adjoint writing z
+// in place over the intermediate, inverse high pass accumulating into the FP64
+// accumulator; then grad = -(w/B) acc and the h partials.
+qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int64_t *row_ptr,
+                        const uint32_t *outcome, const float *c_obs, float2 *grad, cudaStream_t st) {
+    const size_t D = (size_t)1 << p->n;
+    const int tiles = (1 << p->c) / kWideCols;
+    if (cudaMemsetAsync(p->wide_acc, 0, sizeof(double2) * (size_t)p->K * D, st) != cudaSuccess) return QST_ERR_CUDA;
+    for (int g0 = 0; g0 < p->M; g0 += p->wide_G) {
+        const int G = (p->M - g0) < p->wide_G ? (p->M - g0) : p->wide_G;
+        qst_status rc = launch(p, QST_KERNEL_HIGH, st, [&] {
+            k_high_fwd<<<dim3(tiles, G, p->K), 256, 0, st>>>(psi, p->plans, g0, p->K, p->c, p->wide_T);
+        });
+        if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] { k_wide_bins<<<1, 256, 0, st>>>(g0, G, p->bins, p->n_bins); });
+        if (rc) return rc;
+        AdjArgs a;
+        a.psi = p->wide_T;
+        a.plans = p->plans;
+        a.order = p->order;
+        a.bins = p->bins;
+        a.n_bins = p->n_bins;
+        a.row_ptr = row_ptr;
+        a.outcome = outcome;
+        a.c_obs = c_obs;
+        a.choff = p->choff;
+        a.zbuf = p->wide_T;  // each unit reads its chunk before writing its z over it
+        a.src_bin_stride = (int64_t)p->K * (int64_t)D;
+        a.n = p->n;
+        a.r = p->r;
+        a.K = p->K;
+        const int grid = (G << p->r) * p->K;
+        rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
+            with_geo(p->c, p->A, [&](auto cc, auto ra) {
+                constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+                k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true).total, st>>>(a);
+            });
+        });
+        if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] {
+            k_high_inv_acc<<<dim3(tiles, p->K), 256, 0, st>>>(p->wide_T, p->plans, g0, G, p->K, p->c, p->wide_acc);
+        });
+        if (rc) return rc;
+    }
+    const float invB = 1.0f / (float)p->B;
+    const int64_t total = (int64_t)p->K << p->c;
+    return launch(p, QST_KERNEL_REDUCE, st, [&] {
+        k_wide_final<<<(int)((total + 255) / 256), 256, 0, st>>>(p->wide_acc, w, psi, grad, p->hdot, p->n, p->c,
+                                                                 p->K, invB);
     });
 }
 
@@ -1161,10 +1266,15 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     qst_params_default(&prm);
     if (params) prm = *params;
     if (!(prm.eps >= 0.0) || prm.norm_settings < 0 || prm.max_bin_settings < 0) return QST_ERR_INVALID_ARG;
-    int c = prm.chunk_qubits ? prm.chunk_qubits : (n < kMaxChunk ? n : kMaxChunk);
+    if (n > 16 + 4) return QST_ERR_UNSUPPORTED;
+    // n <= 16: chunk min(n, 12), up to 4 binned high bits; n = 17..20: the wide
+    // path with a chunk of n - 8 bits and 8 high bits applied by butterflies.
+    const int c_default = n <= 16 ? (n < kMaxChunk ? n : kMaxChunk) : n - kWideR;
+    int c = prm.chunk_qubits ? prm.chunk_qubits : c_default;
     if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
     const int r = n - c;
-    if (r > kMaxTop) return QST_ERR_UNSUPPORTED;
+    const bool wide = r > kMaxTop;
+    if (wide && (r != kWideR || c < 9)) return QST_ERR_UNSUPPORTED;
     if (K > 4096 || M > (1 << 24) || nnz > ((int64_t)1 << 31) - 1) return QST_ERR_UNSUPPORTED;
     qst_plan p = new (std::nothrow) qst_plan_s;
     if (!p) return QST_ERR_NO_MEMORY;
@@ -1194,9 +1304,16 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         p->smax = (int)(s < 4 ? 4 : s);
     }
     if (p->smax > kMaxBin) p->smax = kMaxBin;
-    const int nkeys = ipow3(r);
-    p->nb_max = (nkeys < M ? nkeys : M) + (M + p->smax - 1) / p->smax;
     const int64_t D = (int64_t)1 << n;
+    if (wide) {
+        p->wide = true;
+        const int64_t g = kWideGroupBytes / (D * (int64_t)K * (int64_t)sizeof(float2));
+        p->wide_G = (int)(g < 1 ? 1 : (g > M ? M : g));
+        p->nb_max = p->wide_G;
+    } else {
+        const int nkeys = ipow3(r);
+        p->nb_max = (nkeys < M ? nkeys : M) + (M + p->smax - 1) / p->smax;
+    }
     p->loss_parts = (M + 7) / 8;  // forward epilogue: one warp per setting, 8 warps per block
     qst_status rc = QST_OK;
     if (!rc) rc = dalloc(p, &p->plans, M);
@@ -1206,7 +1323,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc) rc = dalloc(p, &p->choff, (size_t)M * ((1 << r) + 1));
     if (!rc) rc = dalloc(p, &p->ppart, (size_t)K * nnz);
     if (!rc) rc = dalloc(p, &p->loss_part, p->loss_parts);
-    if (!rc) rc = dalloc(p, &p->zbuf, (size_t)p->nb_max * K * D);
+    if (!rc && !wide) rc = dalloc(p, &p->zbuf, (size_t)p->nb_max * K * D);
+    if (!rc && wide) rc = dalloc(p, &p->wide_T, (size_t)p->wide_G * K * D);
+    if (!rc && wide) rc = dalloc(p, &p->wide_acc, (size_t)K * D);
+    if (!rc && wide) p->zbuf = p->wide_T;
     if (!rc) rc = dalloc(p, &p->hdot, (size_t)K << c);
     if (!rc && K <= kRefacMax) rc = dalloc(p, &p->refac_C, (size_t)K * K);
     if (!rc && K <= kRefacMax) rc = dalloc(p, &p->refac_T, (size_t)K * K);
@@ -1246,7 +1366,9 @@ qst_status qst_plan_destroy(qst_plan p) {
     cudaFree(p->choff);
     cudaFree(p->ppart);
     cudaFree(p->loss_part);
-    cudaFree(p->zbuf);
+    if (!p->wide) cudaFree(p->zbuf);
+    cudaFree(p->wide_T);
+    cudaFree(p->wide_acc);
     cudaFree(p->hdot);
     cudaFree(p->refac_C);
     cudaFree(p->refac_T);
@@ -1289,6 +1411,10 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     if (rc) return rc;
     if (p_dense && cudaMemsetAsync(p_dense, 0, (size_t)p->M * ((size_t)1 << p->n) * sizeof(float), st) != cudaSuccess)
         return QST_ERR_CUDA;
+    if (p->wide) {
+        rc = forward_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, p_dense, st);
+        if (rc) return rc;
+    }
     FwdArgs a;
     a.psi = reinterpret_cast<const float2 *>(psi);
     a.w = w;
@@ -1305,14 +1431,17 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     a.n = p->n;
     a.r = p->r;
     a.K = p->K;
+    a.src_bin_stride = 0;
     const int grid = (p->nb_max << p->r) * p->K;
-    rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
-        with_geo(p->c, p->A, [&](auto cc, auto ra) {
-            constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-            k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
+    if (!p->wide) {
+        rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
+            with_geo(p->c, p->A, [&](auto cc, auto ra) {
+                constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+                k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
+            });
         });
-    });
-    if (rc) return rc;
+        if (rc) return rc;
+    }
     const float invB = 1.0f / (float)p->B;
     const int egrid = p->loss_parts;
     rc = launch(p, QST_KERNEL_EPILOGUE, st, [&] {
@@ -1350,6 +1479,14 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     a.n = p->n;
     a.r = p->r;
     a.K = p->K;
+    a.src_bin_stride = 0;
+    if (p->wide) {
+        rc = adjoint_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, c_obs,
+                          reinterpret_cast<float2 *>(grad_psi), st);
+        if (rc || !grad_w) return rc;
+        const float invBw = 1.0f / (float)p->B;
+        return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w); });
+    }
     const int grid = (p->nb_max << p->r) * p->K;
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
         with_geo(p->c, p->A, [&](auto cc, auto ra) {

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "unsupported size", 3: "CUDA 
                 4: "out of device memory", 5: "device-side error"}
 DEV_BITS = {1: "bad basis code", 2: "malformed CSR counts", 4: "zero shots on a non-empty row",
             8: "non-finite loss"}
-KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue", "refactor"]
+KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue", "refactor", "step",
+                "high"]
 
 
 class QSTError(RuntimeError):

@@ -1,0 +1,93 @@
+"""The wide path (n = 17..20: chunk of n - 8 bits, 8 high bits by butterfly
+passes, settings in groups) against the FP64 oracle, and the n = 20,
+M = 1024, K = 8 workload on sampled outputs and identities."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_19577_b300 import qst, synth
+from test_gpu_parity import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,M,K,shots,seed", [(17, 6, 2, 3000, 1), (18, 4, 2, 4000, 2), (20, 3, 2, 10000, 3)])
+def test_wide_parity(n, M, K, shots, seed):
+    inst = synth.random_instance(n, M, K, shots, 500 + seed)
+    compare(inst, run_gpu(inst), run_oracle(inst))
+
+
+def test_wide_parity_several_groups():
+    """n = 17 puts 64 settings in a group; 70 settings need two groups."""
+    inst = synth.random_instance(17, 70, 1, 500, 77)
+    compare(inst, run_gpu(inst), run_oracle(inst))
+
+
+@pytest.fixture(scope="module")
+def c5():
+    inst = synth.make_instance("n20_m1024_k8", seed=0)
+    plan = qst.Plan(inst.n, inst.M, inst.K, inst.nnz)
+    data = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    psi, w = torch.from_numpy(inst.psi).cuda(), torch.from_numpy(inst.w).cuda()
+    p_obs, c_obs, loss = plan.forward(psi, w, data)
+    g, gw = plan.adjoint(psi, w, data, c_obs)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    yield dict(inst=inst, plan=plan, data=data, psi=psi, w=w, p_obs=p_obs, c_obs=c_obs, loss=loss, g=g, gw=gw)
+    plan.close()
+
+
+def _rows(inst, sel):
+    rp, outs, cnts = [0], [], []
+    for s in sel:
+        lo, hi = inst.row_ptr[s], inst.row_ptr[s + 1]
+        outs.append(inst.outcome[lo:hi])
+        cnts.append(inst.count[lo:hi])
+        rp.append(rp[-1] + hi - lo)
+    return np.array(rp, np.int64), np.concatenate(outs), np.concatenate(cnts)
+
+
+def test_n20_sampled_forward(c5):
+    inst = c5["inst"]
+    sel = synth.rng_for(2024).choice(inst.M, 3, replace=False)
+    rp, out, cnt = _rows(inst, sel)
+    ref = oracle.forward(inst.n, inst.basis[sel], inst.psi.astype(np.complex128), inst.w.astype(np.float64),
+                         rp, out, cnt, inst.shots[sel], eps=inst.eps, B=inst.M)
+    p = c5["p_obs"].cpu().numpy()
+    c = c5["c_obs"].cpu().numpy()
+    for j, s in enumerate(sel):
+        lo, hi = inst.row_ptr[s], inst.row_ptr[s + 1]
+        r = ref["p_obs"][rp[j]:rp[j + 1]]
+        assert np.max(np.abs(p[lo:hi] - r)) / np.max(r) <= 1e-5
+        np.testing.assert_allclose(c[lo:hi], ref["c_obs"][rp[j]:rp[j + 1]], rtol=1e-4)
+
+
+def test_n20_sampled_adjoint(c5):
+    inst = c5["inst"]
+    sel = np.sort(synth.rng_for(7).choice(inst.M, 2, replace=False))
+    mask = np.zeros(inst.nnz, bool)
+    for s in sel:
+        mask[inst.row_ptr[s]:inst.row_ptr[s + 1]] = True
+    c_full = c5["c_obs"].cpu().numpy()
+    g, gw = c5["plan"].adjoint(c5["psi"], c5["w"], c5["data"],
+                               torch.from_numpy(np.where(mask, c_full, 0).astype(np.float32)).cuda())
+    rp, out, _ = _rows(inst, sel)
+    ref = oracle.adjoint(inst.n, inst.basis[sel], inst.psi.astype(np.complex128), inst.w.astype(np.float64),
+                         rp, out, c_full[mask].astype(np.float64), B=inst.M)
+    g = g.cpu().numpy().astype(np.complex128)
+    for k in range(inst.K):
+        assert np.max(np.abs(g[k] - ref["grad_psi"][k])) / np.max(np.abs(ref["grad_psi"][k])) <= 1e-4
+    np.testing.assert_allclose(gw.cpu().numpy(), ref["grad_w"], rtol=1e-4)
+
+
+def test_n20_identities(c5):
+    inst = c5["inst"]
+    psi = c5["psi"].cpu().numpy().astype(np.complex128)
+    w = c5["w"].cpu().numpy().astype(np.float64)
+    g = c5["g"].cpu().numpy().astype(np.complex128)
+    h = -c5["gw"].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(np.sum(np.conj(psi) * (-g / w[:, None]), axis=1).real, h, rtol=1e-4)
+    c = c5["c_obs"].cpu().numpy().astype(np.float64)
+    p = c5["p_obs"].cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(np.dot(w, h), np.sum(c * p / inst.M), rtol=1e-5)
