@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--reg-bits", type=int, default=0, help="amplitudes per thread per round = 2^reg_bits (0 = auto)")
     ap.add_argument("--chunk-qubits", type=int, default=0)
     ap.add_argument("--max-bin-settings", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true", help="time candidate plan layouts first and use the fastest")
     return ap.parse_args()
 
 
@@ -190,11 +191,17 @@ def run_ours(args):
 
     inst = synth.make_instance(args.workload, seed=0)
     n, M, K, D = inst.n, inst.M, inst.K, inst.D
-    plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
-                    max_bin_settings=args.max_bin_settings)
     data = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
     psi = torch.from_numpy(inst.psi).cuda()
     w = torch.from_numpy(inst.w).cuda()
+    tuned = None
+    if args.autotune:
+        best, table = qst.autotune(psi, w, data, eps=inst.eps)
+        args.reg_bits, args.chunk_qubits, args.max_bin_settings = (best["reg_bits"], best["chunk_qubits"],
+                                                                    best["max_bin_settings"])
+        tuned = [{"params": p, "ms": t} for p, t in table]
+    plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
+                    max_bin_settings=args.max_bin_settings)
     p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
     c_obs = torch.empty_like(p_obs)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -324,7 +331,7 @@ def run_ours(args):
                 "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
                            "nnz": int(inst.nnz), "precision_path": "plain FP32",
                            "plan": {"reg_bits": args.reg_bits, "chunk_qubits": args.chunk_qubits,
-                                    "max_bin_settings": args.max_bin_settings},
+                                    "max_bin_settings": args.max_bin_settings, "autotune": tuned},
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),

@@ -400,3 +400,42 @@ class Batch:
 
 def qst_loss(psi, w, plan: Plan, data: Data):
     return QSTLoss.apply(psi, w, plan, data)
+
+
+def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
+    """Pick the fastest plan layout for this problem by timing forward + adjoint
+    (CUDA events on the current stream) over candidate (reg_bits, chunk_qubits,
+    max_bin_settings) triples: 16 or 32 amplitudes per thread and round, the
+    default chunk or one bit smaller, and automatic or fixed bin sizes.
+
+    Returns (best params dict, [(params, ms per evaluation), ...])."""
+    K, D = psi.shape
+    n = D.bit_length() - 1
+    M, nnz = d.M, d.nnz
+    if candidates is None:
+        c0 = n if n <= 12 else (12 if n <= 16 else n - 8)
+        chunks = [0] + ([c0 - 1] if 13 <= n <= 16 and c0 - 1 >= n - 4 else [])
+        candidates = [dict(reg_bits=rb, chunk_qubits=c, max_bin_settings=sm)
+                      for rb in (4, 5) for c in chunks for sm in (0, 32)]
+    results = []
+    for prm in candidates:
+        try:
+            plan = Plan(n, M, K, nnz, eps=eps, **prm)
+        except QSTError:
+            continue
+        _, c_obs, _ = plan.forward(psi, w, d)
+        g, gw = plan.adjoint(psi, w, d, c_obs)
+        for _ in range(warmup):
+            plan.forward(psi, w, d, c_obs=c_obs)
+            plan.adjoint(psi, w, d, c_obs, grad_psi=g, grad_w=gw)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record()
+        for _ in range(reps):
+            plan.forward(psi, w, d, c_obs=c_obs)
+            plan.adjoint(psi, w, d, c_obs, grad_psi=g, grad_w=gw)
+        end.record()
+        torch.cuda.synchronize()
+        results.append((prm, start.elapsed_time(end) / reps))
+        plan.close()
+    results.sort(key=lambda x: x[1])
+    return results[0][0], results

@@ -229,3 +229,12 @@ def test_autograd_function_matches_oracle_gradient():
     fd = (lp - lm) / (2 * t)
     an = float(np.real(np.sum(np.conj(g) * delta)))  # <torch grad, delta> = 2 Re<dL/dpsi^*, delta>
     assert abs(fd - an) <= 1e-3 * max(1.0, abs(fd))
+
+
+def test_autotuner_returns_a_valid_fastest_layout():
+    inst = synth.random_instance(13, 40, 2, 1000, 1300)
+    data = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    psi, w = torch.from_numpy(inst.psi).cuda(), torch.from_numpy(inst.w).cuda()
+    best, table = qst.autotune(psi, w, data, reps=1, warmup=1)
+    assert table and best == table[0][0] and all(t > 0 for _, t in table)
+    compare(inst, run_gpu(inst, **best), run_oracle(inst))
