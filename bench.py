@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--chunk-qubits", type=int, default=0)
     ap.add_argument("--max-bin-settings", type=int, default=0)
     ap.add_argument("--autotune", action="store_true", help="time candidate plan layouts first and use the fastest")
+    ap.add_argument("--per-setting-rounds", action="store_true",
+                    help="choose each setting's rounds (instead of fixed qubit groups for 12-qubit chunks)")
     return ap.parse_args()
 
 
@@ -199,9 +201,10 @@ def run_ours(args):
         best, table = qst.autotune(psi, w, data, eps=inst.eps)
         args.reg_bits, args.chunk_qubits, args.max_bin_settings = (best["reg_bits"], best["chunk_qubits"],
                                                                     best["max_bin_settings"])
+        args.per_setting_rounds = not best["fixed_rounds"]
         tuned = [{"params": p, "ms": t} for p, t in table]
     plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
-                    max_bin_settings=args.max_bin_settings)
+                    max_bin_settings=args.max_bin_settings, fixed_rounds=not args.per_setting_rounds)
     p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
     c_obs = torch.empty_like(p_obs)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -331,7 +334,8 @@ def run_ours(args):
                 "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
                            "nnz": int(inst.nnz), "precision_path": "plain FP32",
                            "plan": {"reg_bits": args.reg_bits, "chunk_qubits": args.chunk_qubits,
-                                    "max_bin_settings": args.max_bin_settings, "autotune": tuned},
+                                    "max_bin_settings": args.max_bin_settings,
+                                    "fixed_rounds": not args.per_setting_rounds, "autotune": tuned},
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),

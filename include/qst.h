@@ -60,6 +60,9 @@ typedef struct qst_params {
     int max_bin_settings; /* cap on settings per work bin; 0 = auto */
     int validate;         /* 1 = check basis and CSR on the device (default 1) */
     int reg_bits;         /* amplitudes per thread per round = 2^reg_bits: 4 or 5; 0 = auto */
+    int fixed_rounds;     /* 1 = 12-qubit chunks with 16 amplitudes per thread run three rounds on
+                             fixed qubit groups (compile-time shared-memory offsets, warp-local
+                             middle exchange); 0 = rounds chosen per setting (default 1) */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;

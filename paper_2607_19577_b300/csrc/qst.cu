@@ -94,6 +94,10 @@ __device__ __forceinline__ uint32_t phys(uint32_t u) {
     return u ^ (((u >> 4) ^ (u >> 8)) & 15u);
 }
 
+// Padded index of the fixed-round kernels (one spare element per 16): additive
+// over disjoint bit sets, fx_pidx(a | b) = fx_pidx(a) + fx_pidx(b).
+__host__ __device__ constexpr uint32_t fx_pidx(uint32_t u) { return u + (u >> 4); }
+
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -531,10 +535,11 @@ __device__ __forceinline__ void build_lut(const SetPlan &P, uint32_t *lut, uint3
 }
 
 // Chunk f of (U_h (x) I) psi_k, written to shared memory "i-major": register
-// element i of thread t (amplitude t + i 2^TB) at index i 2^TB + t.  U_h is
+// element i of thread t (amplitude t + i 2^TB) at index i 2^TB + t (at
+// fx_pidx of it for the fixed-round kernels).  U_h is
 // the unscaled product of the high-bit factors, with the same rows as the
 // butterflies (Z factors select f'_j = f_j).
-template <int C, int RA>
+template <int C, int RA, bool kPadded = false>
 __device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, uint32_t f,
                                              uint32_t xytop, uint32_t ytop, uint32_t tid) {
     using G = Geo<C, RA>;
@@ -586,7 +591,10 @@ __device__ __forceinline__ void build_source(float2 *src, const float2 *__restri
         }
     }
 #pragma unroll
-    for (int i = 0; i < G::E; ++i) src[(i << G::TB) + tid] = acc[i];
+    for (int i = 0; i < G::E; ++i) {
+        const uint32_t u = (uint32_t)(i << G::TB) + tid;
+        src[kPadded ? fx_pidx(u) : u] = acc[i];
+    }
 }
 
 // Forward rounds of one setting's chunk transform.  On return v holds the
@@ -962,6 +970,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 
 #include "qst_update.cuh"
 #include "qst_wide.cuh"
+#include "qst_fixed.cuh"
 
 // ----------------------------------------------------------------- host side
 
@@ -981,6 +990,7 @@ struct TimedLaunch {
 struct qst_plan_s {
     int n = 0, M = 0, K = 0, c = 0, r = 0, A = 0, T = 0, smax = 0, nb_max = 0, B = 0;
     bool wide = false;       // n = 17..20: high bits by butterfly passes, groups of wide_G settings
+    bool fx = false;         // 12-qubit chunks with fixed-position rounds (k_forward_fx / k_adjoint_fx)
     int wide_G = 0;
     float2 *wide_T = nullptr;    // [wide_G][K][D] intermediate (also the z buffer)
     double2 *wide_acc = nullptr; // [K][D] FP64 accumulator of G psi
@@ -1118,6 +1128,28 @@ void with_geo(int c, int ra, Fn &&fn) {
     }
 }
 
+// The plan's forward / adjoint chunk kernel over `grid` work units.
+void launch_forward_units(qst_plan p, const FwdArgs &a, int grid, cudaStream_t st) {
+    if (p->fx) {
+        k_forward_fx<<<grid, kFxT, fx_smem(false).total, st>>>(a);
+        return;
+    }
+    with_geo(p->c, p->A, [&](auto cc, auto ra) {
+        constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+        k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
+    });
+}
+void launch_adjoint_units(qst_plan p, const AdjArgs &a, int grid, cudaStream_t st) {
+    if (p->fx) {
+        k_adjoint_fx<<<grid, kFxT, fx_smem(true).total, st>>>(a);
+        return;
+    }
+    with_geo(p->c, p->A, [&](auto cc, auto ra) {
+        constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+        k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true).total, st>>>(a);
+    });
+}
+
 qst_status prepare(qst_plan p, const uint8_t *basis, const int64_t *row_ptr, const uint32_t *outcome,
                    const uint32_t *shots, cudaStream_t st) {
     qst_status rc = launch(p, QST_KERNEL_PACK, st, [&] {
@@ -1170,10 +1202,7 @@ qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.K = p->K;
         const int grid = (G << p->r) * p->K;
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
-            with_geo(p->c, p->A, [&](auto cc, auto ra) {
-                constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-                k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
-            });
+            launch_forward_units(p, a, grid, st);
         });
         if (rc) return rc;
     }
@@ -1212,10 +1241,7 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.K = p->K;
         const int grid = (G << p->r) * p->K;
         rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
-            with_geo(p->c, p->A, [&](auto cc, auto ra) {
-                constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-                k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true).total, st>>>(a);
-            });
+            launch_adjoint_units(p, a, grid, st);
         });
         if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] {
             k_high_inv_acc<<<dim3(tiles, p->K), 256, 0, st>>>(p->wide_T, p->plans, g0, G, p->K, p->c, p->wide_acc);
@@ -1242,6 +1268,7 @@ void qst_params_default(qst_params *p) {
     p->max_bin_settings = 0;
     p->validate = 1;
     p->reg_bits = 0;
+    p->fixed_rounds = 1;
 }
 
 const char *qst_status_string(qst_status s) {
@@ -1292,6 +1319,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
+    p->fx = c == 12 && p->A == 4 && prm.fixed_rounds != 0;
     p->B = prm.norm_settings ? prm.norm_settings : M;
     cudaGetDevice(&p->device);
     int sms = 148;
@@ -1347,6 +1375,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) {
         with_geo(p->c, p->A, [](auto cc, auto ra) { set_smem_attrs<decltype(cc)::value, decltype(ra)::value>(); });
+        if (p->fx) {
+            cudaFuncSetAttribute(k_forward_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(false).total);
+            cudaFuncSetAttribute(k_adjoint_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
+        }
         if (cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
     }
     if (rc) {
@@ -1435,10 +1467,7 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     const int grid = (p->nb_max << p->r) * p->K;
     if (!p->wide) {
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
-            with_geo(p->c, p->A, [&](auto cc, auto ra) {
-                constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-                k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
-            });
+            launch_forward_units(p, a, grid, st);
         });
         if (rc) return rc;
     }
@@ -1489,10 +1518,7 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     }
     const int grid = (p->nb_max << p->r) * p->K;
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
-        with_geo(p->c, p->A, [&](auto cc, auto ra) {
-            constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
-            k_adjoint<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true).total, st>>>(a);
-        });
+        launch_adjoint_units(p, a, grid, st);
     });
     if (rc) return rc;
     const float invB = 1.0f / (float)p->B;

@@ -38,7 +38,7 @@ class QSTError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm_settings", ctypes.c_int),
                 ("chunk_qubits", ctypes.c_int), ("max_bin_settings", ctypes.c_int),
-                ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int)]
+                ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int), ("fixed_rounds", ctypes.c_int)]
 
 
 class _StepParams(ctypes.Structure):
@@ -146,13 +146,13 @@ class Plan:
     """Owns a qst_plan (device workspace for one problem shape)."""
 
     def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
-                 max_bin_settings=0, validate=True, reg_bits=0):
+                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=True):
         lib = load()
         prm = _Params()
         lib.qst_params_default(ctypes.byref(prm))
         prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
         prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
-        prm.reg_bits = int(reg_bits)
+        prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(bool(fixed_rounds))
         h = ctypes.c_void_p()
         _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
                "qst_plan_create")
@@ -405,8 +405,9 @@ def qst_loss(psi, w, plan: Plan, data: Data):
 def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
     """Pick the fastest plan layout for this problem by timing forward + adjoint
     (CUDA events on the current stream) over candidate (reg_bits, chunk_qubits,
-    max_bin_settings) triples: 16 or 32 amplitudes per thread and round, the
-    default chunk or one bit smaller, and automatic or fixed bin sizes.
+    max_bin_settings, fixed_rounds) choices: 16 or 32 amplitudes per thread and
+    round, the default chunk or one bit smaller, automatic or fixed bin sizes,
+    and fixed-group or per-setting rounds.
 
     Returns (best params dict, [(params, ms per evaluation), ...])."""
     K, D = psi.shape
@@ -415,8 +416,9 @@ def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
     if candidates is None:
         c0 = n if n <= 12 else (12 if n <= 16 else n - 8)
         chunks = [0] + ([c0 - 1] if 13 <= n <= 16 and c0 - 1 >= n - 4 else [])
-        candidates = [dict(reg_bits=rb, chunk_qubits=c, max_bin_settings=sm)
-                      for rb in (4, 5) for c in chunks for sm in (0, 32)]
+        candidates = [dict(reg_bits=rb, chunk_qubits=c, max_bin_settings=sm, fixed_rounds=fx)
+                      for rb in (4, 5) for c in chunks for sm in (0, 32) for fx in (True, False)
+                      if not (fx and rb == 5)]
     results = []
     for prm in candidates:
         try:

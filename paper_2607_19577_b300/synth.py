@@ -202,11 +202,17 @@ def make_instance(name: str, seed: int = 0, probs_fn=None, n=None, M=None, shots
                     w=w.astype(np.float32), truth_w=tw, truth_atoms=ta)
 
 
-def random_instance(n: int, M: int, K: int, shots: int, seed: int, dense_frac: float = None) -> Instance:
+def random_instance(n: int, M: int, K: int, shots: int, seed: int, dense_frac: float = None,
+                    basis: np.ndarray = None) -> Instance:
     """A small instance with surrogate counts, random atoms and Dirichlet weights
-    (used for parity sweeps over shapes)."""
+    (used for parity sweeps over shapes).  `basis` ([M][n] codes) replaces the
+    random Pauli strings when given."""
     rng = rng_for(seed, 7)
-    basis = pauli_settings(n, M, rng)
+    if basis is None:
+        basis = pauli_settings(n, M, rng)
+    else:
+        basis = np.ascontiguousarray(basis, dtype=np.uint8)
+        M = basis.shape[0]
     tw = dirichlet_weights(max(1, min(K, 4)), rng)
     shots_arr = np.full(M, shots, dtype=np.uint32)
     row_ptr, outcome, count = surrogate_counts(n, shots_arr, tw, rng_for(seed, 8))

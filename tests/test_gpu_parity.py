@@ -238,3 +238,23 @@ def test_autotuner_returns_a_valid_fastest_layout():
     best, table = qst.autotune(psi, w, data, reps=1, warmup=1)
     assert table and best == table[0][0] and all(t > 0 for _, t in table)
     compare(inst, run_gpu(inst, **best), run_oracle(inst))
+
+
+@pytest.mark.parametrize("n,fixed", [(12, True), (12, False), (13, True), (13, False), (16, True), (16, False)])
+def test_parity_fixed_and_per_setting_rounds(n, fixed):
+    """12-qubit chunks run either the fixed-group rounds (bits 8..11, 4..7,
+    0..3) or rounds chosen per setting; both against the oracle, with settings
+    whose whole 4-qubit groups are Z (skipped rounds), all-X, all-Y and random."""
+    rng = synth.rng_for(700 + n)
+    M_rand = 14
+    special = []
+    for q0 in (0, 4, 8):                      # chunk bits q0..q0+3 all Z, the rest random X/Y
+        row = rng.integers(1, 3, n).astype(np.uint8)
+        for b in range(q0, q0 + 4):
+            row[n - 1 - b] = 0                # qubit n-1-b carries outcome bit b
+        special.append(row)
+    special += [np.zeros(n, np.uint8), np.ones(n, np.uint8), np.full(n, 2, np.uint8)]
+    basis = np.concatenate([np.stack(special), synth.pauli_settings(n, M_rand, rng)])
+    inst = synth.random_instance(n, basis.shape[0], 3, 800, 710 + n, basis=basis)
+    dense = n <= 12
+    compare(inst, run_gpu(inst, dense=dense, fixed_rounds=fixed), run_oracle(inst, dense=dense), dense=dense)
