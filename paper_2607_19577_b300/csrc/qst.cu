@@ -534,18 +534,17 @@ __device__ __forceinline__ void build_lut(const SetPlan &P, uint32_t *lut, uint3
     }
 }
 
-// Chunk f of (U_h (x) I) psi_k, written to shared memory "i-major": register
-// element i of thread t (amplitude t + i 2^TB) at index i 2^TB + t (at
-// fx_pidx of it for the fixed-round kernels).  U_h is
-// the unscaled product of the high-bit factors, with the same rows as the
-// butterflies (Z factors select f'_j = f_j).
-template <int C, int RA, bool kPadded = false>
-__device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, uint32_t f,
-                                             uint32_t xytop, uint32_t ytop, uint32_t tid) {
+// Chunk f of (U_h (x) I) psi_k in registers: element i of thread t is
+// amplitude t + i 2^TB of the chunk.  U_h is the unscaled product of the
+// high-bit factors, with the same rows as the butterflies (Z factors select
+// f'_j = f_j).  Only elements I0 .. I0 + NI - 1 are built (a caller short of
+// registers builds the chunk in parts).
+template <int C, int RA, int I0 = 0, int NI = Geo<C, RA>::E>
+__device__ __forceinline__ void build_source_regs(float2 (&acc)[Geo<C, RA>::E], const float2 *__restrict__ psik,
+                                                  uint32_t f, uint32_t xytop, uint32_t ytop, uint32_t tid) {
     using G = Geo<C, RA>;
-    float2 acc[G::E];
 #pragma unroll
-    for (int i = 0; i < G::E; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = I0; i < I0 + NI; ++i) acc[i] = make_float2(0.f, 0.f);
     const int nx = __popc(xytop);
     // coefficient phase i^ph of source chunk f' in output chunk f
     auto chunk = [&](int idx, int &ph) {
@@ -567,34 +566,41 @@ __device__ __forceinline__ void build_source(float2 *src, const float2 *__restri
     for (; idx + 1 < nidx; idx += 2) {  // two chunks in flight per step
         int ph0, ph1;
         const float2 *b0 = chunk(idx, ph0), *b1 = chunk(idx + 1, ph1);
-        float2 x0[G::E], x1[G::E];
+        float2 x0[NI], x1[NI];
 #pragma unroll
-        for (int i = 0; i < G::E; ++i) {
-            x0[i] = __ldg(b0 + (i << G::TB));
-            x1[i] = __ldg(b1 + (i << G::TB));
+        for (int i = 0; i < NI; ++i) {
+            x0[i] = __ldg(b0 + ((I0 + i) << G::TB));
+            x1[i] = __ldg(b1 + ((I0 + i) << G::TB));
         }
 #pragma unroll
-        for (int i = 0; i < G::E; ++i) {
+        for (int i = 0; i < NI; ++i) {
             const float2 y0 = mul_ipow(x0[i], ph0), y1 = mul_ipow(x1[i], ph1);
-            acc[i].x += y0.x + y1.x;
-            acc[i].y += y0.y + y1.y;
+            acc[I0 + i].x += y0.x + y1.x;
+            acc[I0 + i].y += y0.y + y1.y;
         }
     }
     if (idx < nidx) {
         int ph0;
         const float2 *b0 = chunk(idx, ph0);
 #pragma unroll
-        for (int i = 0; i < G::E; ++i) {
+        for (int i = I0; i < I0 + NI; ++i) {
             const float2 y0 = mul_ipow(__ldg(b0 + (i << G::TB)), ph0);
             acc[i].x += y0.x;
             acc[i].y += y0.y;
         }
     }
+}
+
+// The same chunk written to shared memory "i-major": register element i of
+// thread t at index i 2^TB + t.
+template <int C, int RA>
+__device__ __forceinline__ void build_source(float2 *src, const float2 *__restrict__ psik, uint32_t f,
+                                             uint32_t xytop, uint32_t ytop, uint32_t tid) {
+    using G = Geo<C, RA>;
+    float2 acc[G::E];
+    build_source_regs<C, RA>(acc, psik, f, xytop, ytop, tid);
 #pragma unroll
-    for (int i = 0; i < G::E; ++i) {
-        const uint32_t u = (uint32_t)(i << G::TB) + tid;
-        src[kPadded ? fx_pidx(u) : u] = acc[i];
-    }
+    for (int i = 0; i < G::E; ++i) src[(i << G::TB) + tid] = acc[i];
 }
 
 // Forward rounds of one setting's chunk transform.  On return v holds the
