@@ -180,7 +180,7 @@ def run_reference(args):
 
 def run_ours(args):
     import torch
-    from paper_2607_19577_b300 import qst, synth
+    from paper_2607_19577_b300 import qst, replicas, synth
 
     ws, rank, local = dist_env()
     if not torch.cuda.is_available():
@@ -246,13 +246,11 @@ def run_ours(args):
     plan.set_timing(False)
     plan.check()
     ms_total = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
     amps_step = M * K * D
-    value = amps_step * ws / (ms_step / 1e3)
+    # slowest rank's time, every rank's units (each rank runs one replica)
+    ms_total, amps_all = replicas.aggregate(ms_total, amps_step, dist, device="cuda")
+    ms_step = ms_total / args.steps
+    value = amps_all / (ms_step / 1e3)
 
     # roofline of the dominant kernel (the adjoint)
     fwd_ops, adj_ops = algorithmic_ops(inst.basis, K, D)
@@ -309,13 +307,10 @@ def run_ours(args):
             t0 = time.perf_counter()
             plan.evaluate_host_buffers(h_psi, *h, out=outs, stream=stream.cuda_stream)
             t_e2e += time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e, _ = replicas.aggregate(t_e2e, amps_step, dist, device="cuda")
         h2d = h_psi.nbytes + sum(a.nbytes for a in h)
         d2h = outs[0].nbytes + outs[1].nbytes + outs[2].nbytes
-        e2e = {"value": amps_step * ws / (t_e2e / args.steps), "unit": "amplitudes/s",
+        e2e = {"value": amps_all / (t_e2e / args.steps), "unit": "amplitudes/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * t_e2e / args.steps}
 
