@@ -116,9 +116,15 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """sha256 over the CUDA sources (qst.cu and its headers, in name order)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2607_19577_b300", "csrc", "qst.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2607_19577_b300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()
 
 
 def algorithmic_ops(basis, K, D):
@@ -254,6 +260,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the adjoint)
     fwd_ops, adj_ops = algorithmic_ops(inst.basis, K, D)
+    geo = plan.geometry()
     # per-step kernel time (the wide path launches its chunk kernels once per setting group)
     la, ms_adj = stats["adjoint"]
     lf, ms_fwd = stats["forward"]
@@ -273,12 +280,14 @@ def run_ours(args):
         try:
             rec = json.load(open(prof))
             # counters only count for the kernel source they were taken on
-            if rec.get("source_sha256") == kernel_source_hash() and rec.get("workload") == args.workload:
+            if (rec.get("source_sha256") == kernel_source_hash() and rec.get("workload") == args.workload
+                    and rec.get("kernel") == ("k_adjoint_fx" if geo["fixed_rounds"] else "k_adjoint")):
                 traffic = rec.get("bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                "frac": achieved / peak_alu, "traffic": traffic, "kernel": "k_adjoint",
+                "frac": achieved / peak_alu, "traffic": traffic,
+                "kernel": "k_adjoint_fx" if geo["fixed_rounds"] else "k_adjoint",
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                "(max SM clock of MEASURED_PEAKS.json)",
                 "ops_per_launch": adj_ops, "ms_per_launch": adj_ms,
@@ -330,7 +339,7 @@ def run_ours(args):
                            "nnz": int(inst.nnz), "precision_path": "plain FP32",
                            "plan": {"reg_bits": args.reg_bits, "chunk_qubits": args.chunk_qubits,
                                     "max_bin_settings": args.max_bin_settings,
-                                    "fixed_rounds": not args.per_setting_rounds, "autotune": tuned},
+                                    "geometry": geo, "autotune": tuned},
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),

@@ -88,6 +88,12 @@ qst_status qst_plan_destroy(qst_plan plan);
 /* Bytes of device workspace the plan holds. */
 qst_status qst_plan_workspace_bytes(qst_plan plan, int64_t *bytes);
 
+/* The plan's chunk geometry: qubits transformed on-chip per work unit, high
+ * qubits applied outside the chunk (by setting bins, or by butterfly passes
+ * for n = 17..20), and whether the fixed-group round kernels run (1) or the
+ * per-setting ones (0).  Any output pointer may be NULL.  Host only. */
+qst_status qst_plan_geometry(qst_plan plan, int *chunk_qubits, int *high_qubits, int *fixed_rounds);
+
 /*
  * Forward pass (Eqs. atom-response, atomic-born-map, qst-loss,
  * likelihood-ratio-vector):

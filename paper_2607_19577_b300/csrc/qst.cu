@@ -1435,6 +1435,14 @@ qst_status qst_plan_workspace_bytes(qst_plan p, int64_t *bytes) {
     return QST_OK;
 }
 
+qst_status qst_plan_geometry(qst_plan p, int *chunk_qubits, int *high_qubits, int *fixed_rounds) {
+    if (!p) return QST_ERR_INVALID_ARG;
+    if (chunk_qubits) *chunk_qubits = p->c;
+    if (high_qubits) *high_qubits = p->r;
+    if (fixed_rounds) *fixed_rounds = p->fx ? 1 : 0;
+    return QST_OK;
+}
+
 qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8_t *basis, const int64_t *row_ptr,
                        const uint32_t *outcome, const uint32_t *count, const uint32_t *shots, float *p_obs,
                        float *c_obs, double *loss, float *p_dense, void *stream) {

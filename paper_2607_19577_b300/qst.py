@@ -64,6 +64,7 @@ def load():
         lib.qst_plan_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, i64, ctypes.POINTER(_Params)]
         lib.qst_plan_destroy.argtypes = [P]
         lib.qst_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(i64)]
+        lib.qst_plan_geometry.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.qst_forward.argtypes = [P] + [P] * 11 + [P]
         lib.qst_adjoint.argtypes = [P] + [P] * 8 + [P]
         lib.qst_evaluate_host.argtypes = [P] + [P] * 11 + [P]
@@ -83,7 +84,7 @@ def load():
         lib.qst_step_params_default.restype = None
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
                                  ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
-        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_forward",
+        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_forward",
                      "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
@@ -174,6 +175,12 @@ class Plan:
         v = ctypes.c_int64()
         _check(load().qst_plan_workspace_bytes(self._h, ctypes.byref(v)), "workspace_bytes")
         return v.value
+
+    def geometry(self):
+        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan."""
+        c, r, fx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().qst_plan_geometry(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(fx)), "geometry")
+        return {"chunk_qubits": c.value, "high_qubits": r.value, "fixed_rounds": bool(fx.value)}
 
     def _data(self, d: Data):
         _need(d.basis, torch.uint8, (self.M, self.n), "basis")
