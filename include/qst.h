@@ -143,6 +143,20 @@ qst_status qst_evaluate_host(qst_plan plan, const float *psi, const float *w,
                              float *grad_psi_out, float *grad_w_out,
                              float *c_obs_out, void *stream);
 
+/*
+ * Projected descent direction of every atom (Sec. III-A, Eq.
+ * atom-projected-descent-direction): d_k = w_k (I - psi_k psi_k^*) G psi_k,
+ * formed from qst_adjoint's outputs as d_k = -grad_k + w_k grad_w_k psi_k
+ * (grad_k = -w_k G psi_k, grad_w_k = -h_k with h_k = <psi_k|G psi_k>
+ * accumulated in FP64 by the adjoint).  For a unit-norm psi_k, d_k is
+ * orthogonal to psi_k.
+ *   psi, grad_psi [K][2^n] complex64, w, grad_w [K] float32 (device, read)
+ *   d [K][2^n] complex64 (device, written; may alias grad_psi)
+ * One elementwise kernel on the stream (memory-bound).
+ */
+qst_status qst_tangent(qst_plan plan, const float *psi, const float *w, const float *grad_psi,
+                       const float *grad_w, float *d, void *stream);
+
 /* Synchronise the device and read (then clear) the plan's device status word.
  * Returns QST_ERR_DEVICE if any bit was set (bits in *device_status). */
 qst_status qst_plan_status(qst_plan plan, int *device_status);
@@ -163,7 +177,8 @@ enum {
     QST_KERNEL_REFACTOR = 8,
     QST_KERNEL_STEP = 9,
     QST_KERNEL_HIGH = 10,
-    QST_KERNEL_KINDS = 11
+    QST_KERNEL_TANGENT = 11,
+    QST_KERNEL_KINDS = 12
 };
 qst_status qst_plan_set_timing(qst_plan plan, int enable);
 qst_status qst_plan_kernel_stats(qst_plan plan, int64_t *launches, double *ms,

@@ -771,6 +771,19 @@ __global__ void __launch_bounds__(256) k_fwd_epilogue(const float *__restrict__ 
     if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
 }
 
+// d_k = -grad_k + w_k grad_w_k psi_k = w_k (I - psi_k psi_k^*) G psi_k
+// (Eq. atom-projected-descent-direction), one thread per amplitude.
+__global__ void __launch_bounds__(256) k_tangent(const float2 *__restrict__ psi, const float *__restrict__ w,
+                                                 const float2 *grad, const float *__restrict__ gw, float2 *d,
+                                                 int n, int K) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ((int64_t)K << n)) return;
+    const int k = (int)(idx >> n);
+    const float s = w[k] * gw[k];
+    const float2 g = grad[idx], x = psi[idx];
+    d[idx] = make_float2(fmaf(s, x.x, -g.x), fmaf(s, x.y, -g.y));
+}
+
 struct AdjArgs {
     const float2 *psi;
     const SetPlan *plans;
@@ -1433,6 +1446,20 @@ qst_status qst_plan_workspace_bytes(qst_plan p, int64_t *bytes) {
     if (!p || !bytes) return QST_ERR_INVALID_ARG;
     *bytes = p->ws_bytes;
     return QST_OK;
+}
+
+qst_status qst_tangent(qst_plan p, const float *psi, const float *w, const float *grad_psi, const float *grad_w,
+                       float *d, void *stream) {
+    if (!p || !psi || !w || !grad_psi || !grad_w || !d) return QST_ERR_INVALID_ARG;
+    if (!aligned(psi, 8) || !aligned(grad_psi, 8) || !aligned(d, 8) || !aligned(w, 4) || !aligned(grad_w, 4))
+        return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t total = (int64_t)p->K << p->n;
+    return launch(p, QST_KERNEL_TANGENT, st, [&] {
+        k_tangent<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+            reinterpret_cast<const float2 *>(psi), w, reinterpret_cast<const float2 *>(grad_psi), grad_w,
+            reinterpret_cast<float2 *>(d), p->n, p->K);
+    });
 }
 
 qst_status qst_plan_geometry(qst_plan p, int *chunk_qubits, int *high_qubits, int *fixed_rounds) {

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "unsupported size", 3: "CUDA 
 DEV_BITS = {1: "bad basis code", 2: "malformed CSR counts", 4: "zero shots on a non-empty row",
             8: "non-finite loss"}
 KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue", "refactor", "step",
-                "high"]
+                "high", "tangent"]
 
 
 class QSTError(RuntimeError):
@@ -65,6 +65,7 @@ def load():
         lib.qst_plan_destroy.argtypes = [P]
         lib.qst_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(i64)]
         lib.qst_plan_geometry.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.qst_tangent.argtypes = [P, P, P, P, P, P, P]
         lib.qst_forward.argtypes = [P] + [P] * 11 + [P]
         lib.qst_adjoint.argtypes = [P] + [P] * 8 + [P]
         lib.qst_evaluate_host.argtypes = [P] + [P] * 11 + [P]
@@ -84,7 +85,7 @@ def load():
         lib.qst_step_params_default.restype = None
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
                                  ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
-        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_forward",
+        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_tangent", "qst_forward",
                      "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
@@ -175,6 +176,18 @@ class Plan:
         v = ctypes.c_int64()
         _check(load().qst_plan_workspace_bytes(self._h, ctypes.byref(v)), "workspace_bytes")
         return v.value
+
+    def tangent(self, psi, w, grad_psi, grad_w, out=None):
+        """d_k = w_k (I - psi_k psi_k^*) G psi_k from the adjoint's outputs (out may be grad_psi)."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(grad_psi, torch.complex64, (self.K, self.D), "grad_psi")
+        _need(w, torch.float32, (self.K,), "w")
+        _need(grad_w, torch.float32, (self.K,), "grad_w")
+        out = torch.empty_like(grad_psi) if out is None else out
+        _need(out, torch.complex64, (self.K, self.D), "out")
+        _check(load().qst_tangent(self._h, _ptr(psi), _ptr(w), _ptr(grad_psi), _ptr(grad_w), _ptr(out), _stream()),
+               "qst_tangent")
+        return out
 
     def geometry(self):
         """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan."""

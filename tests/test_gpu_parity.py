@@ -258,3 +258,32 @@ def test_parity_fixed_and_per_setting_rounds(n, fixed):
     inst = synth.random_instance(n, basis.shape[0], 3, 800, 710 + n, basis=basis)
     dense = n <= 12
     compare(inst, run_gpu(inst, dense=dense, fixed_rounds=fixed), run_oracle(inst, dense=dense), dense=dense)
+
+
+@pytest.mark.parametrize("n,M,K,seed", [(5, 14, 3, 0), (12, 20, 4, 1), (16, 6, 2, 2)])
+def test_tangent_matches_oracle(n, M, K, seed):
+    """qst_tangent (Eq. atom-projected-descent-direction) from the adjoint's outputs,
+    against the oracle's d_k = w_k (I - psi_k psi_k^*) G psi_k; for unit-norm atoms
+    d_k is orthogonal to psi_k."""
+    inst = synth.random_instance(n, M, K, 800, 1200 + seed)
+    psi = inst.psi.astype(np.complex128)
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    inst.psi = psi.astype(np.complex64)
+    plan = qst.Plan(n, inst.M, K, inst.nnz, eps=inst.eps)
+    d = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    tp, tw = torch.from_numpy(inst.psi).cuda(), torch.from_numpy(inst.w).cuda()
+    _, c_obs, _ = plan.forward(tp, tw, d)
+    g, gw = plan.adjoint(tp, tw, d, c_obs)
+    t = plan.tangent(tp, tw, g, gw).cpu().numpy().astype(np.complex128)
+    ref = run_oracle(inst)
+    want = oracle.tangent(inst.psi.astype(np.complex128), inst.w.astype(np.float64), ref["G_psi"])
+    for k in range(K):
+        # normwise against the size of the terms that are subtracted (w_k G psi_k)
+        nrm = max(np.max(np.abs(want[k])), inst.w[k] * np.max(np.abs(ref["G_psi"][k])))
+        assert np.max(np.abs(t[k] - want[k])) / nrm <= G_TOL
+        p = inst.psi[k].astype(np.complex128)
+        assert abs(np.vdot(p, t[k])) <= 1e-4 * np.linalg.norm(t[k])
+    # aliasing the output onto grad_psi gives the same result
+    t2 = plan.tangent(tp, tw, g, gw, out=g).cpu().numpy().astype(np.complex128)
+    np.testing.assert_array_equal(t2, t)
+    plan.close()
