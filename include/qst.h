@@ -252,6 +252,38 @@ qst_status qst_step(qst_plan plan, int slot, int r, float *psi, float *w,
                     double *J_out, int *accepted, double *eta_used, void *stream);
 
 /*
+ * T iterations t = t0 .. t0 + T - 1 of Algorithm 1 (Sec. III-D) on the state
+ * (psi, w), with every decision taken on the device and no host
+ * synchronisation inside.  Iteration t is a refactor slot when T_ref > 0 and
+ * (t + 1) mod T_ref == 0, else a coefficient slot when (t + 1) mod
+ * T_alpha == 0, else an atom slot on r_t = the (s mod R_t)-th atom with
+ * w > 0, s counting the atom slots since t = 0 (the cyclic choice; a run with
+ * t0 > 0 continues the count of the previous run on this plan).  Each slot
+ * does what qst_step does for that slot (same kernels, same step grid, first
+ * accepted trial kept), so a run equals the matching sequence of qst_step
+ * calls exactly.
+ *   J_hist [T] double (device, written): J = L_eps + mu R after each iteration
+ *   accepted_hist [T] int (device, written, may be NULL): 1 if the iteration moved
+ * The whole launch sequence (packing, the starting J, then per iteration
+ * adjoint, trials, forwards, acceptance, commit) is captured into a CUDA graph
+ * on the first call with given pointers, T, t0 schedule and parameters, and
+ * replayed on the stream afterwards.  Settings and counts must not change
+ * between replays without new pointers.  n <= 16 (binned path); refactor
+ * slots need K <= 32.
+ */
+typedef struct qst_iter_params {
+    qst_step_params step;  /* mu, tau, tau_acc, step grid (qst_step_params_default) */
+    int T_alpha;           /* coefficient slots: (t + 1) mod T_alpha == 0 (default 5) */
+    int T_ref;             /* refactor slots: (t + 1) mod T_ref == 0 (default 50; 0 = never) */
+} qst_iter_params;
+void qst_iter_params_default(qst_iter_params *ip);
+qst_status qst_iterate(qst_plan plan, int T, int t0, float *psi, float *w,
+                       const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const uint32_t *count,
+                       const uint32_t *shots, const qst_iter_params *params,
+                       double *J_hist, int *accepted_hist, void *stream);
+
+/*
  * Batched evaluation of many independent instances of uneven shape (the
  * batched workload of the benchmark spec: instances with different n, M, K and
  * shots).  qst_batch_create makes one plan per instance (params shared).

@@ -656,6 +656,7 @@ struct FwdArgs {
     float *p_dense;    // optional [M][D] (accumulated with atomics; zeroed by the host)
     int64_t nnz;
     int64_t src_bin_stride;  // elements between the sources of consecutive bins (0: all bins read psi)
+    const int *skip;         // optional device flag: when set, the launch does nothing
     int n, r, K;
 };
 
@@ -681,7 +682,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
     const int rest = unit / a.K;
     const uint32_t f = rest & ((1u << a.r) - 1u);
     const int bin = rest >> a.r;
-    if (bin >= *a.n_bins) return;
+    if (bin >= *a.n_bins || (a.skip && *a.skip)) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
     constexpr uint32_t cmask = G::N - 1;
@@ -745,7 +746,8 @@ __global__ void __launch_bounds__(256) k_fwd_epilogue(const float *__restrict__ 
                                                       const uint32_t *__restrict__ shots,
                                                       int M, int K, int64_t nnz, float invB, float eps,
                                                       float *__restrict__ p_obs, float *__restrict__ c_obs,
-                                                      double *__restrict__ loss_part) {
+                                                      double *__restrict__ loss_part, const int *skip) {
+    if (skip && *skip) return;
     __shared__ double red[kRedMax];
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -976,7 +978,8 @@ __global__ void __launch_bounds__(256) k_hsum(const double *__restrict__ hdot, i
 
 // loss = sum of the forward epilogue's per-block partial sums (FP64, fixed order).
 __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_part, int parts,
-                                              double *__restrict__ loss, int *__restrict__ status) {
+                                              double *__restrict__ loss, int *__restrict__ status, const int *skip) {
+    if (skip && *skip) return;
     __shared__ double red[kRedMax];
     double s = 0.0;
     for (int u = threadIdx.x; u < parts; u += blockDim.x) s += loss_part[u];
@@ -990,6 +993,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_update.cuh"
 #include "qst_wide.cuh"
 #include "qst_fixed.cuh"
+#include "qst_iterate.cuh"
 
 // ----------------------------------------------------------------- host side
 
@@ -1039,6 +1043,13 @@ struct qst_plan_s {
     double *step_loss = nullptr;   // [1]
     int *step_kout = nullptr;      // [1]
     int *status = nullptr;
+    // qst_iterate: device state, trial likelihood ratio, captured graph
+    IterState *it_state = nullptr;
+    float *it_c = nullptr;
+    cudaStream_t it_cap = nullptr;
+    cudaGraphExec_t it_exec = nullptr;
+    std::vector<double> it_key;
+    int64_t it_launches = 0;
     int64_t ws_bytes = 0;
     // host-buffer path (allocated on first use)
     void *h_dev = nullptr;
@@ -1216,6 +1227,7 @@ qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.p_dense = p_dense;
         a.nnz = p->nnz;
         a.src_bin_stride = (int64_t)p->K * (int64_t)D;
+        a.skip = nullptr;
         a.n = p->n;
         a.r = p->r;
         a.K = p->K;
@@ -1275,6 +1287,11 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
     });
 }
 
+qst_status forward_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
+                        const uint32_t *count, const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
+                        float *p_dense, const int *skip, cudaStream_t st);
+qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
+                        const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st);
 }  // namespace
 
 extern "C" {
@@ -1385,6 +1402,9 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc) rc = dalloc(p, &p->step_m1, K);
     if (!rc) rc = dalloc(p, &p->step_loss, 1);
     if (!rc) rc = dalloc(p, &p->step_kout, 1);
+    if (!rc) rc = dalloc(p, &p->it_state, 1);
+    if (!rc && cudaMemset(p->it_state, 0, sizeof(IterState)) != cudaSuccess) rc = QST_ERR_CUDA;
+    if (!rc) rc = dalloc(p, &p->it_c, nnz);
     if (!rc) {
         std::vector<float> m1((size_t)K, -1.0f);
         if (cudaMemcpy(p->step_m1, m1.data(), sizeof(float) * K, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1433,6 +1453,10 @@ qst_status qst_plan_destroy(qst_plan p) {
     cudaFree(p->step_kout);
     cudaFree(p->status);
     cudaFree(p->h_dev);
+    cudaFree(p->it_state);
+    cudaFree(p->it_c);
+    if (p->it_exec) cudaGraphExecDestroy(p->it_exec);
+    if (p->it_cap) cudaStreamDestroy(p->it_cap);
     for (auto &tl : p->pending) {
         cudaEventDestroy(tl.start);
         cudaEventDestroy(tl.stop);
@@ -1482,6 +1506,18 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     cudaStream_t st = (cudaStream_t)stream;
     qst_status rc = prepare(p, basis, row_ptr, outcome, shots, st);
     if (rc) return rc;
+    return forward_core(p, psi, w, row_ptr, outcome, count, shots, p_obs, c_obs, loss, p_dense, nullptr, st);
+}
+
+}  // extern "C"
+
+namespace {
+// The forward after packing and validation; with `skip` set on the device
+// (optional) every launch returns at once.
+qst_status forward_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
+                        const uint32_t *count, const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
+                        float *p_dense, const int *skip, cudaStream_t st) {
+    qst_status rc = QST_OK;
     if (p_dense && cudaMemsetAsync(p_dense, 0, (size_t)p->M * ((size_t)1 << p->n) * sizeof(float), st) != cudaSuccess)
         return QST_ERR_CUDA;
     if (p->wide) {
@@ -1505,6 +1541,7 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     a.r = p->r;
     a.K = p->K;
     a.src_bin_stride = 0;
+    a.skip = skip;
     const int grid = (p->nb_max << p->r) * p->K;
     if (!p->wide) {
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
@@ -1516,13 +1553,16 @@ qst_status qst_forward(qst_plan p, const float *psi, const float *w, const uint8
     const int egrid = p->loss_parts;
     rc = launch(p, QST_KERNEL_EPILOGUE, st, [&] {
         k_fwd_epilogue<<<egrid, 256, 0, st>>>(p->ppart, row_ptr, count, shots, p->M, p->K, p->nnz, invB,
-                                              (float)p->prm.eps, p_obs, c_obs, p->loss_part);
+                                              (float)p->prm.eps, p_obs, c_obs, p->loss_part, skip);
     });
     if (rc) return rc;
     return launch(p, QST_KERNEL_LOSS, st, [&] {
-        k_loss<<<1, 256, 0, st>>>(p->loss_part, p->loss_parts, loss, p->status);
+        k_loss<<<1, 256, 0, st>>>(p->loss_part, p->loss_parts, loss, p->status, skip);
     });
 }
+}  // namespace
+
+extern "C" {
 
 qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8_t *basis, const int64_t *row_ptr,
                        const uint32_t *outcome, const float *c_obs, float *grad_psi, float *grad_w, void *stream) {
@@ -1535,6 +1575,16 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
     // shots are only validated in the forward; the adjoint reads c directly
     qst_status rc = prepare(p, basis, row_ptr, outcome, nullptr, st);
     if (rc) return rc;
+    return adjoint_core(p, psi, w, row_ptr, outcome, c_obs, grad_psi, grad_w, st);
+}
+
+}  // extern "C"
+
+namespace {
+// The adjoint after packing and validation.
+qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
+                        const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st) {
+    qst_status rc = QST_OK;
     AdjArgs a;
     a.psi = reinterpret_cast<const float2 *>(psi);
     a.plans = p->plans;
@@ -1580,6 +1630,9 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
         k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invB, grad_w);
     });
 }
+}  // namespace
+
+extern "C" {
 
 qst_status qst_evaluate_host(qst_plan p, const float *psi, const float *w, const uint8_t *basis,
                              const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
@@ -1763,11 +1816,11 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
         if (rc) return rc;
         if (cudaMemcpyAsync(trial_psi, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return QST_ERR_CUDA;
-        const float2 *psr = reinterpret_cast<const float2 *>(psi) + (size_t)r * D;
         float2 *out = p->step_trial + (size_t)r * D;
         for (int j = 0; j < sp.n_eta; ++j, eta *= sp.eta_ratio) {
             rc = launch(p, QST_KERNEL_STEP, st, [&] {
-                k_atom_trial<<<1, 1024, 0, st>>>(psr, p->step_grad + (size_t)r * D, wh[r], eta, (int64_t)D, out);
+                k_atom_trial<<<1, 1024, 0, st>>>(reinterpret_cast<const float2 *>(psi), p->step_grad, w, nullptr, r,
+                                                 eta, (int64_t)D, p->step_trial, nullptr);
             });
             if (rc) return rc;
             double Jt = 0.0;
@@ -1793,7 +1846,7 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
     if (rc) return rc;
     for (int j = 0; j < sp.n_eta; ++j, eta *= sp.eta_ratio) {
         rc = launch(p, QST_KERNEL_STEP, st, [&] {
-            k_coeff_trial<<<1, kProjMax, 0, st>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw);
+            k_coeff_trial<<<1, kProjMax, 0, st>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw, nullptr);
         });
         if (rc) return rc;
         double Jt = 0.0;
@@ -1810,6 +1863,161 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
         }
     }
     *eta_used = eta / sp.eta_ratio;
+    return QST_OK;
+}
+
+void qst_iter_params_default(qst_iter_params *ip) {
+    if (!ip) return;
+    qst_step_params_default(&ip->step);
+    ip->T_alpha = 5;
+    ip->T_ref = 50;
+}
+
+}  // extern "C"
+
+namespace {
+// Slot of iteration t (0 = atom, 1 = coefficients, 2 = refactor).
+int iter_slot(const qst_iter_params &ip, int64_t t) {
+    if (ip.T_ref > 0 && (t + 1) % ip.T_ref == 0) return 2;
+    if (ip.T_alpha > 0 && (t + 1) % ip.T_alpha == 0) return 1;
+    return 0;
+}
+
+// The launch sequence of qst_iterate on stream s (captured by the caller).
+qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, const uint8_t *basis,
+                            const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
+                            const uint32_t *shots, const qst_iter_params &ip, double *J_hist, int *acc_hist,
+                            cudaStream_t s) {
+    const qst_step_params &sp = ip.step;
+    const int K = p->K;
+    const int64_t D = (int64_t)1 << p->n;
+    float2 *ps = reinterpret_cast<float2 *>(psi);
+    float *trial = reinterpret_cast<float *>(p->step_trial);
+    float *grad = reinterpret_cast<float *>(p->step_grad);
+    const int *done = &p->it_state->done;
+    const int *rdev = &p->it_state->r;
+    qst_status rc = prepare(p, basis, row_ptr, outcome, shots, s);
+    if (!rc) rc = forward_core(p, psi, w, row_ptr, outcome, count, shots, nullptr, p->step_c, p->step_loss, nullptr,
+                               nullptr, s);
+    if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
+        k_iter_init<<<1, 32, 0, s>>>(p->it_state, p->step_loss, w, K, sp.mu, t0 == 0 ? 1 : 0);
+    });
+    const int cgrid = 148 * 4;
+    for (int i = 0; i < T && !rc; ++i) {
+        const int slot = iter_slot(ip, (int64_t)t0 + i);
+        rc = launch(p, QST_KERNEL_STEP, s, [&] { k_iter_begin<<<1, 32, 0, s>>>(p->it_state, w, K, slot); });
+        if (rc) break;
+        double eta = sp.eta0;
+        if (slot == 0) {  // atom r_t along its projected direction (Eqs. atom-direction, atom-trial)
+            rc = adjoint_core(p, psi, p->step_m1, row_ptr, outcome, p->step_c, grad, nullptr, s);
+            if (!rc && cudaMemcpyAsync(trial, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                rc = QST_ERR_CUDA;
+            for (int j = 0; j < sp.n_eta && !rc; ++j, eta *= sp.eta_ratio) {
+                rc = launch(p, QST_KERNEL_STEP, s, [&] {
+                    k_atom_trial<<<1, 1024, 0, s>>>(ps, p->step_grad, w, rdev, 0, eta, D, p->step_trial, done);
+                });
+                if (!rc) rc = forward_core(p, trial, w, row_ptr, outcome, count, shots, nullptr, p->it_c, p->step_loss,
+                                           nullptr, done, s);
+                if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
+                    k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, w, K, sp.mu, sp.tau_acc, j, eta);
+                });
+            }
+        } else if (slot == 1) {  // coefficients (Eq. coefficient-update, then P_tau)
+            rc = adjoint_core(p, psi, w, row_ptr, outcome, p->step_c, grad, p->step_gw, s);
+            for (int j = 0; j < sp.n_eta && !rc; ++j, eta *= sp.eta_ratio) {
+                rc = launch(p, QST_KERNEL_STEP, s, [&] {
+                    k_coeff_trial<<<1, kProjMax, 0, s>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw, done);
+                });
+                if (!rc) rc = forward_core(p, psi, p->step_tw, row_ptr, outcome, count, shots, nullptr, p->it_c,
+                                           p->step_loss, nullptr, done, s);
+                if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
+                    k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, p->step_tw, K, sp.mu, sp.tau_acc, j, eta);
+                });
+            }
+        } else {  // exact spectral refactorisation (eta_rho = 0)
+            if (cudaMemcpyAsync(trial, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(p->step_tw, w, sizeof(float) * K, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                rc = QST_ERR_CUDA;
+            if (!rc) rc = qst_refactor(p, trial, p->step_tw, sp.tau, p->step_kout, s);
+            if (!rc) rc = forward_core(p, trial, p->step_tw, row_ptr, outcome, count, shots, nullptr, p->it_c,
+                                       p->step_loss, nullptr, nullptr, s);
+            if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
+                k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, p->step_tw, K, sp.mu, sp.tau_acc, 0, 0.0);
+            });
+        }
+        if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
+            k_iter_commit<<<cgrid, 256, 0, s>>>(p->it_state, slot, p->step_trial, p->step_tw, ps, w, K, D, p->it_c,
+                                                p->step_c, p->nnz);
+        });
+        if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
+            k_iter_end<<<1, 32, 0, s>>>(p->it_state, J_hist, acc_hist, i);
+        });
+    }
+    return rc;
+}
+}  // namespace
+
+extern "C" {
+
+qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const uint32_t *count, const uint32_t *shots,
+                       const qst_iter_params *params, double *J_hist, int *accepted_hist, void *stream) {
+    if (!p || T < 1 || t0 < 0 || !psi || !w || !basis || !row_ptr || !shots || !J_hist) return QST_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!outcome || !count)) return QST_ERR_INVALID_ARG;
+    if (!aligned(psi, 16) || !aligned(w, 4) || !aligned(J_hist, 8) || (accepted_hist && !aligned(accepted_hist, 4)))
+        return QST_ERR_INVALID_ARG;
+    qst_iter_params ip;
+    qst_iter_params_default(&ip);
+    if (params) ip = *params;
+    const qst_step_params &sp = ip.step;
+    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0) || ip.T_alpha < 0 || ip.T_ref < 0)
+        return QST_ERR_INVALID_ARG;
+    if (p->wide || p->K > kProjMax) return QST_ERR_UNSUPPORTED;
+    for (int i = 0; i < T; ++i)
+        if (iter_slot(ip, (int64_t)t0 + i) == 2 && !p->refac_C) return QST_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the graph depends on the pointers, T, the schedule phase of t0 and the parameters
+    const int64_t period = (int64_t)(ip.T_alpha > 0 ? ip.T_alpha : 1) * (ip.T_ref > 0 ? ip.T_ref : 1);
+    std::vector<double> key = {(double)(uintptr_t)psi, (double)(uintptr_t)w, (double)(uintptr_t)basis,
+                               (double)(uintptr_t)row_ptr, (double)(uintptr_t)outcome, (double)(uintptr_t)count,
+                               (double)(uintptr_t)shots, (double)(uintptr_t)J_hist, (double)(uintptr_t)accepted_hist,
+                               (double)T, (double)(t0 == 0 ? -1 : t0 % period), sp.mu, sp.tau, sp.tau_acc, sp.eta0,
+                               sp.eta_ratio, (double)sp.n_eta, (double)ip.T_alpha, (double)ip.T_ref};
+    if (!p->it_exec || key != p->it_key) {
+        if (p->it_exec) {
+            cudaGraphExecDestroy(p->it_exec);
+            p->it_exec = nullptr;
+        }
+        if (!p->it_cap && cudaStreamCreateWithFlags(&p->it_cap, cudaStreamNonBlocking) != cudaSuccess)
+            return QST_ERR_CUDA;
+        const bool timing = p->timing;
+        const int64_t before = p->total_launches;
+        p->timing = false;  // no event records inside the graph
+        if (cudaStreamBeginCapture(p->it_cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            p->timing = timing;
+            return QST_ERR_CUDA;
+        }
+        qst_status rc = iterate_sequence(p, T, t0, psi, w, basis, row_ptr, outcome, count, shots, ip, J_hist,
+                                         accepted_hist, p->it_cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(p->it_cap, &g);
+        p->timing = timing;
+        p->it_launches = p->total_launches - before;
+        p->total_launches = before;
+        if (rc || ce != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : QST_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&p->it_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            p->it_exec = nullptr;
+            return QST_ERR_CUDA;
+        }
+        p->it_key = key;
+    }
+    if (cudaGraphLaunch(p->it_exec, st) != cudaSuccess) return QST_ERR_CUDA;
+    p->total_launches += p->it_launches;
     return QST_OK;
 }
 

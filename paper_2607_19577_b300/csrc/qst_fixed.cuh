@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
     const int rest = unit / a.K;
     const uint32_t f = rest & ((1u << a.r) - 1u);
     const int bin = rest >> a.r;
-    if (bin >= *a.n_bins) return;
+    if (bin >= *a.n_bins || (a.skip && *a.skip)) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
     constexpr uint32_t cmask = 4095u;

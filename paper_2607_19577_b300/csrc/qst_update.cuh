@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kProjMax) k_simplex(const double *__restrict__
 // h = -grad_w; inactive and pruned atoms get weight 0.  One CTA, K <= kProjMax.
 __global__ void __launch_bounds__(kProjMax) k_coeff_trial(const float *__restrict__ w,
                                                           const float *__restrict__ grad_w, double eta,
-                                                          double tau, int K, float *__restrict__ w_out) {
+                                                          double tau, int K, float *__restrict__ w_out,
+                                                          const int *skip) {
+    if (skip && *skip) return;  // a trial of this slot was already accepted
     __shared__ SimplexSmem sm;
     __shared__ int idx[kProjMax];
     __shared__ double beta[kProjMax];
@@ -116,10 +118,18 @@ __global__ void __launch_bounds__(kProjMax) k_coeff_trial(const float *__restric
 // Atom trial of a T_psi slot (Eqs. atom-direction, atom-trial): with
 // G psi_r given, g = w_r (G psi_r - psi_r <psi_r, G psi_r>) and
 // out = (psi_r + eta g) / ||psi_r + eta g||.  One CTA; FP64 reductions in a
-// fixed order.
-__global__ void __launch_bounds__(1024) k_atom_trial(const float2 *__restrict__ psi_r,
-                                                     const float2 *__restrict__ gpsi_r, float wr, double eta,
-                                                     int64_t D, float2 *__restrict__ out) {
+// fixed order.  The atom is r_dev[0] when r_dev is given (chosen on the
+// device), else r_host; skip as in k_coeff_trial.
+__global__ void __launch_bounds__(1024) k_atom_trial(const float2 *__restrict__ psi, const float2 *__restrict__ gpsi,
+                                                     const float *__restrict__ w, const int *r_dev, int r_host,
+                                                     double eta, int64_t D, float2 *__restrict__ out_all,
+                                                     const int *skip) {
+    if (skip && *skip) return;
+    const int r = r_dev ? *r_dev : r_host;
+    const float2 *__restrict__ psi_r = psi + (size_t)r * D;
+    const float2 *__restrict__ gpsi_r = gpsi + (size_t)r * D;
+    float2 *__restrict__ out = out_all + (size_t)r * D;
+    const float wr = w[r];
     __shared__ double red[1024];
     __shared__ double inr_sm, ini_sm, nrm_sm;
     const int t = threadIdx.x;

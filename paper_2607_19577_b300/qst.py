@@ -46,6 +46,10 @@ class _StepParams(ctypes.Structure):
                 ("eta0", ctypes.c_double), ("eta_ratio", ctypes.c_double), ("n_eta", ctypes.c_int)]
 
 
+class _IterParams(ctypes.Structure):
+    _fields_ = [("step", _StepParams), ("T_alpha", ctypes.c_int), ("T_ref", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -66,6 +70,9 @@ def load():
         lib.qst_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(i64)]
         lib.qst_plan_geometry.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.qst_tangent.argtypes = [P, P, P, P, P, P, P]
+        lib.qst_iter_params_default.argtypes = [ctypes.POINTER(_IterParams)]
+        lib.qst_iter_params_default.restype = None
+        lib.qst_iterate.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_IterParams), P, P, P]
         lib.qst_forward.argtypes = [P] + [P] * 11 + [P]
         lib.qst_adjoint.argtypes = [P] + [P] * 8 + [P]
         lib.qst_evaluate_host.argtypes = [P] + [P] * 11 + [P]
@@ -85,7 +92,7 @@ def load():
         lib.qst_step_params_default.restype = None
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
                                  ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
-        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_tangent", "qst_forward",
+        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_tangent", "qst_iterate", "qst_forward",
                      "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
@@ -282,6 +289,26 @@ class Plan:
                                _ptr(d.outcome), _ptr(d.count), _ptr(d.shots), ctypes.byref(sp), ctypes.byref(J),
                                ctypes.byref(acc), ctypes.byref(eta), _stream()), "qst_step")
         return J.value, bool(acc.value), eta.value
+
+    def iterate(self, T, t0, psi, w, d: Data, J_hist=None, accepted=None, T_alpha=5, T_ref=50, **step_params):
+        """qst_iterate: T iterations of Algorithm 1 from iteration t0, in place on psi
+        and w, every decision on the device (one CUDA graph, replayed on later calls
+        with the same buffers).  Returns device tensors (J_hist float64 [T],
+        accepted int32 [T]); nothing is synchronised."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(w, torch.float32, (self.K,), "w")
+        self._data(d)
+        ip = _IterParams()
+        load().qst_iter_params_default(ctypes.byref(ip))
+        ip.T_alpha, ip.T_ref = int(T_alpha), int(T_ref)
+        for k, v in step_params.items():
+            setattr(ip.step, k, v)
+        J_hist = torch.empty(T, dtype=torch.float64, device="cuda") if J_hist is None else J_hist
+        accepted = torch.empty(T, dtype=torch.int32, device="cuda") if accepted is None else accepted
+        _check(load().qst_iterate(self._h, int(T), int(t0), _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr),
+                                  _ptr(d.outcome), _ptr(d.count), _ptr(d.shots), ctypes.byref(ip), _ptr(J_hist),
+                                  _ptr(accepted), _stream()), "qst_iterate")
+        return J_hist, accepted
 
     def status(self):
         """Synchronise and return the device status bits (0 = clean)."""

@@ -118,3 +118,61 @@ def test_step_sequence_matches_oracle():
         # continue the oracle from the GPU state (FP32), so differences do not accumulate
         op, ow = gp, gw
     plan.close()
+
+
+def _schedule(t, T_alpha, T_ref):
+    if T_ref > 0 and (t + 1) % T_ref == 0:
+        return 2
+    if T_alpha > 0 and (t + 1) % T_alpha == 0:
+        return 1
+    return 0
+
+
+@pytest.mark.parametrize("name,n,K,T,T_alpha,T_ref", [("n4_all81", None, 4, 14, 3, 7),
+                                                       ("n12_m60_k6", 12, 6, 9, 4, 0)])
+def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref):
+    """qst_iterate (every decision on the device, one captured graph) equals the same
+    schedule driven from the host with qst_step: bitwise the same atoms and weights
+    and the same J after every iteration.  A second run continues (t0 = T) and a
+    replay of the first run's graph on the same buffers reproduces it."""
+    inst = synth.make_instance(name, seed=11, K=K)
+    psi0 = inst.psi.astype(np.complex128)
+    psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
+    psi0 = psi0.astype(np.complex64)
+    w0 = inst.w.astype(np.float32)
+    plan = qst.Plan(inst.n, inst.M, K, inst.nnz)
+    d = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    # host-driven reference
+    hp, hw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
+    Jh, acc_h, count = [], [], 0
+    for t in range(2 * T):
+        slot = _schedule(t, T_alpha, T_ref)
+        r = 0
+        if slot == 0:
+            act = [k for k, v in enumerate(hw.cpu().numpy()) if v > 0]
+            r = act[count % len(act)]
+            count += 1
+        J, acc, _ = plan.step(slot, r, hp, hw, d)
+        Jh.append(J)
+        acc_h.append(acc)
+    # device-driven: first T iterations, a replay of the same graph from the
+    # same start, then the next T iterations (t0 = T continues the atom cycle)
+    dp, dw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
+    J1, a1 = plan.iterate(T, 0, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref)
+    first = (J1.cpu().numpy().copy(), a1.cpu().numpy().copy(), dp.clone(), dw.clone())
+    dp.copy_(torch.from_numpy(psi0))
+    dw.copy_(torch.from_numpy(w0))
+    J1, a1 = plan.iterate(T, 0, dp, dw, d, J_hist=J1, accepted=a1, T_alpha=T_alpha, T_ref=T_ref)
+    torch.cuda.synchronize()
+    assert np.array_equal(J1.cpu().numpy(), first[0]) and np.array_equal(a1.cpu().numpy(), first[1])
+    assert torch.equal(dp, first[2]) and torch.equal(dw, first[3])
+    J2, a2 = plan.iterate(T, T, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref)
+    torch.cuda.synchronize()
+    plan.check()
+    Jd = list(first[0]) + list(J2.cpu().numpy())
+    ad = list(first[1]) + list(a2.cpu().numpy())
+    assert [bool(x) for x in ad] == acc_h
+    assert Jd == Jh
+    assert torch.equal(dp, hp) and torch.equal(dw, hw)
+    assert sum(acc_h) > 0
+    plan.close()
