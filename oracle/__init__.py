@@ -227,8 +227,83 @@ def objective(n, data, psi, w, eps, mu):
     return f["loss"] + mu * R, f
 
 
+def _orth_block(W, drop, scale):
+    """Orthonormal rows spanning the rows of W: from the Gram matrix
+    C_ij = <w_i, w_j> = V Lambda V^*, u_j = sum_i V_ij w_i / sqrt(lambda_j) for the
+    eigenvalues lambda_j > drop * scale (scale: the squared Frobenius norm of the
+    block before any projection), sorted descending."""
+    C = W.conj() @ W.T
+    lam, V = np.linalg.eigh(C)
+    order = np.argsort(lam)[::-1]
+    lam, V = lam[order], V[:, order]
+    keep = lam > drop * scale
+    return (V[:, keep] / np.sqrt(lam[keep])[None, :]).T @ W
+
+
+def krylov_ritz(n, data, psi, w, c_obs, eta, n_krylov=32, drop=1e-10, B=None):
+    """Ritz pairs of S = Psi diag(w) Psi^* + eta G (Eqs. density-proposal,
+    density-product, ritz-pairs) from a block Krylov space started at the atoms
+    (the block of K vectors; one product with G per block, as the adjoint gives):
+      Q_0 = orth(Psi);  W = S Q_j minus its components on every previous block,
+      taken twice (full reorthogonalisation);  Q_{j+1} = orth(W);
+    while the basis stays within n_krylov vectors.  Rayleigh-Ritz on
+    T = Q^* S Q (Hermitian part).  A block direction is dropped when its squared
+    norm after the projections is below drop times the block's squared norm
+    before them.  Returns (lam descending, Phi [m][D] Ritz vectors)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    w = np.asarray(w, dtype=np.float64)
+    K = psi.shape[0]
+
+    def S(V):  # rows of V are vectors
+        G = apply_G(n, data["basis"], data["row_ptr"], data["outcome"], c_obs, V, B)
+        rho = (psi.T @ (w[:, None] * (psi.conj() @ V.T))).T
+        return rho + eta * G
+
+    blocks = [_orth_block(psi, drop, float(np.sum(np.abs(psi) ** 2)))]
+    sblocks = []
+    while True:
+        SQ = S(blocks[-1])
+        sblocks.append(SQ)
+        m = sum(b.shape[0] for b in blocks)
+        if m + K > n_krylov or blocks[-1].shape[0] == 0:
+            break
+        W = SQ.copy()
+        for _ in range(2):
+            for Qb in blocks:
+                W = W - (Qb.conj() @ W.T).T @ Qb
+        Qn = _orth_block(W, drop, float(np.sum(np.abs(SQ) ** 2)))
+        if Qn.shape[0] == 0:
+            break
+        blocks.append(Qn)
+    Q = np.vstack(blocks)
+    SQ = np.vstack(sblocks[:len(blocks)])
+    T = Q.conj() @ SQ.T
+    T = 0.5 * (T + T.conj().T)
+    lam, Y = np.linalg.eigh(T)
+    order = np.argsort(lam)[::-1]
+    lam, Y = lam[order], Y[:, order]
+    return lam, Y.T @ Q
+
+
+def spectral_candidates(lam, eta, mu, tau, L):
+    """Candidates of Eq. spectral-candidates and their scores (Eq.
+    proximal-surrogate): for s = 1..L, beta = P_tau(proj_Delta(lam_1..s)); with
+    orthonormal Ritz vectors ||rho_X - S||_F^2 = ||beta||^2 - 2 beta^T lam_I + ||S||_F^2,
+    and the last term is the same for every candidate, so
+    Q_s = (||beta||^2 - 2 beta^T lam_I) / (2 eta) + mu |I|.  Returns
+    (s* (1-based, first minimum), [(kept indices, weights, Q_s) for s = 1..L])."""
+    out = []
+    for s_ in range(1, L + 1):
+        beta = simplex_project(lam[:s_])
+        keep, b = prune(beta, tau)
+        q = (np.dot(b, b) - 2.0 * np.dot(b, lam[keep])) / (2.0 * eta) + mu * keep.size
+        out.append((keep, b, q))
+    qs = [c[2] for c in out]
+    return int(np.argmin(qs)) + 1, out
+
+
 def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, eta0=1.0, eta_ratio=0.5,
-         n_eta=11):
+         n_eta=11, n_krylov=32):
     """One slot of Algorithm 1 with the step grid of Sec. IV (eta = eta0 * eta_ratio^j,
     j = 0..n_eta-1, largest first; the first accepted proposal is kept) and the
     acceptance rule J(X~) <= J_t - tau_acc (Eq. state-acceptance-rule).
@@ -238,6 +313,9 @@ def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, e
              coefficient-update), then P_tau.
       slot 2 (T_rho): the exact spectral refactorisation of rho_t (eta_rho = 0), then P_tau;
              one proposal, no step grid.
+      slot 3 (T_rho): the spectral step of Sec. III-C with eta_rho from the step grid:
+             Ritz pairs of S_t = rho_t + eta G_t (krylov_ritz), candidates and their
+             scores (spectral_candidates, L_t = K), the best candidate, acceptance.
     Zero-weight slots are inactive.  Returns (psi, w, J, accepted, eta)."""
     psi = np.array(psi, dtype=np.complex128)
     w = np.array(w, dtype=np.float64)
@@ -254,6 +332,20 @@ def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, e
         if Jt <= J0 - tau_acc:
             return pt, wt, Jt, True, 0.0
         return psi, w, J0, False, 0.0
+    if slot == 3:
+        K = psi.shape[0]
+        for eta in etas:
+            lam, Phi = krylov_ritz(n, data, psi, w, f0["c_obs"], eta, n_krylov)
+            s_star, cands = spectral_candidates(lam, eta, mu, tau, min(K, lam.size))
+            keep, b, _ = cands[s_star - 1]
+            pt = np.zeros_like(psi)
+            wt = np.zeros_like(w)
+            pt[:keep.size] = Phi[keep]
+            wt[:keep.size] = b
+            Jt, _ = objective(n, data, pt, wt, eps, mu)
+            if Jt <= J0 - tau_acc:
+                return pt, wt, Jt, True, eta
+        return psi, w, J0, False, etas[-1]
     adj = adjoint(n, data["basis"], psi, w, data["row_ptr"], data["outcome"], f0["c_obs"])
     if slot == 0:
         g = tangent(psi[r:r + 1], w[r:r + 1], adj["G_psi"][r:r + 1])[0]

@@ -112,3 +112,120 @@ def test_oracle_atom_step_decreases_loss_for_small_eta():
     pt[0] = t / np.linalg.norm(t)
     J1, _ = oracle.objective(5, data, pt, w, 1e-8, 1e-3)
     assert J1 < J0
+
+
+# ----------------------------------------------------------------- spectral step (Sec. III-C)
+
+def _dense_S(inst, psi, w, c_obs, eta):
+    """S = Psi diag(w) Psi^* + eta sum_m c_m E_m with E_m from Kronecker products of
+    the single-qubit eigenbases (a route independent of the oracle's butterflies)."""
+    from test_oracle_pins import dense_rotation
+    D = 1 << inst.n
+    M = inst.basis.shape[0]
+    G = np.zeros((D, D), complex)
+    for s in range(M):
+        U = dense_rotation(inst.basis[s])
+        for i in range(inst.row_ptr[s], inst.row_ptr[s + 1]):
+            u = int(inst.outcome[i])
+            G += c_obs[i] * np.outer(U[u].conj(), U[u]) / M
+    rho = (psi.T * w) @ psi.conj()
+    return rho + eta * G
+
+
+def _spectral_setup(seed=3, K=4):
+    inst = synth.make_instance("n4_all81", seed=seed, K=K)
+    psi = inst.psi.astype(np.complex128)
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    w = inst.w.astype(np.float64)
+    f = oracle.forward(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    return inst, psi, w, f["c_obs"]
+
+
+@pytest.mark.parametrize("eta", [1.0, 0.25, 1e-3])
+def test_krylov_ritz_spanning_the_space_gives_the_dense_eigenpairs(eta):
+    """At n = 4 the block Krylov space reaches all of C^16, so its Ritz pairs are the
+    eigenpairs of the dense S (Eq. ritz-pairs with zero residual)."""
+    inst, psi, w, c = _spectral_setup()
+    lam, Phi = oracle.krylov_ritz(inst.n, _data(inst), psi, w, c, eta)
+    S = _dense_S(inst, psi, w, c, eta)
+    assert lam.size == 16
+    np.testing.assert_allclose(lam, np.sort(np.linalg.eigvalsh(S))[::-1], atol=1e-12)
+    np.testing.assert_allclose(Phi.conj() @ Phi.T, np.eye(16), atol=1e-12)
+    res = np.linalg.norm((S @ Phi.T).T - lam[:, None] * Phi, axis=1)
+    assert res.max() < 1e-11
+
+
+def test_krylov_ritz_partial_space_is_rayleigh_ritz():
+    """With fewer Krylov vectors than D the Ritz values interlace the spectrum: the
+    largest Ritz value lies below the largest eigenvalue, and every Ritz value is a
+    Rayleigh quotient of its unit Ritz vector."""
+    inst, psi, w, c = _spectral_setup()
+    lam, Phi = oracle.krylov_ritz(inst.n, _data(inst), psi, w, c, 0.5, n_krylov=8)
+    S = _dense_S(inst, psi, w, c, 0.5)
+    assert lam.size == 8
+    ev = np.sort(np.linalg.eigvalsh(S))[::-1]
+    assert lam[0] <= ev[0] + 1e-12 and lam[-1] >= ev[-1] - 1e-12
+    rq = np.real(np.einsum("id,de,ie->i", Phi.conj(), S, Phi))
+    np.testing.assert_allclose(rq, lam, atol=1e-12)
+
+
+def _frob2(a, b):
+    return float(np.sum(np.abs(a - b) ** 2))
+
+
+@pytest.mark.parametrize("eta", [1.0, 0.1])
+def test_spectral_candidates_theorem_1(eta):
+    """Theorem 1 with exact eigenpairs and tau = 0: (i) candidate s minimises
+    ||rho_X - S||_F over feasible X of rank <= s (checked against many random
+    feasible states); (ii) the selected candidate minimises Q_t over all of them;
+    and the A15 score equals the dense Frobenius form up to the constant ||S||^2."""
+    inst, psi, w, c = _spectral_setup()
+    K, mu = psi.shape[0], 1e-3
+    lam, Phi = oracle.krylov_ritz(inst.n, _data(inst), psi, w, c, eta)
+    S = _dense_S(inst, psi, w, c, eta)
+    s_star, cands = oracle.spectral_candidates(lam, eta, mu, 0.0, K)
+    rng = np.random.default_rng(0)
+    Qfull = []
+    for s_, (keep, b, q) in enumerate(cands, start=1):
+        rho_x = (Phi[keep].T * b) @ Phi[keep].conj()
+        f2 = _frob2(rho_x, S)
+        np.testing.assert_allclose(q, (f2 - _frob2(0 * S, S)) / (2 * eta) + mu * keep.size, rtol=1e-10, atol=1e-12)
+        Qfull.append(f2 / (2 * eta) + mu * keep.size)
+        for _ in range(200):  # random feasible states of rank <= s
+            R = int(rng.integers(1, s_ + 1))
+            A = rng.standard_normal((R, 16)) + 1j * rng.standard_normal((R, 16))
+            A /= np.linalg.norm(A, axis=1, keepdims=True)
+            a = rng.dirichlet(np.ones(R))
+            rho_r = (A.T * a) @ A.conj()
+            assert _frob2(rho_r, S) >= f2 - 1e-12
+            assert _frob2(rho_r, S) / (2 * eta) + mu * R >= min(Qfull) - 1e-12 or s_ < s_star
+    assert int(np.argmin(Qfull)) + 1 == s_star
+
+
+def test_spectral_step_small_eta_reduces_to_the_refactor():
+    """As eta -> 0, S_t -> rho_t and the spectral candidate with the most atoms is the
+    exact eigen-refactorisation of rho_t."""
+    inst, psi, w, c = _spectral_setup()
+    K = psi.shape[0]
+    lam, Phi = oracle.krylov_ritz(inst.n, _data(inst), psi, w, c, 1e-9)
+    _, cands = oracle.spectral_candidates(lam, 1e-9, 0.0, 1e-3, K)
+    keep, b, _ = cands[-1]
+    phi, wk = oracle.refactor(psi, w, 1e-3)
+    np.testing.assert_allclose(b, wk, atol=1e-6)
+    rho_a = (Phi[keep].T * b) @ Phi[keep].conj()
+    rho_b = (phi.T * wk) @ phi.conj()
+    assert _frob2(rho_a, rho_b) < 1e-10
+
+
+def test_oracle_spectral_slot_is_monotone_and_feasible():
+    inst, psi, w, _ = _spectral_setup(seed=5)
+    data = _data(inst)
+    J_prev = None
+    for slot in (3, 0, 1, 3):
+        psi, w, J, acc, eta = oracle.step(inst.n, data, psi, w, slot, 0)
+        assert np.all(w >= 0) and abs(w.sum() - 1) < 1e-12
+        act = w > 0
+        np.testing.assert_allclose(np.linalg.norm(psi[act], axis=1), 1.0, atol=1e-12)
+        if J_prev is not None:
+            assert J <= J_prev + 1e-15
+        J_prev = J
