@@ -231,7 +231,16 @@ qst_status qst_refactor(qst_plan plan, float *psi, float *w, double tau,
  *          h = A^T c (Eqs. h_t, coefficient-update), then P_tau.
  *   slot 2 (T_rho): the exact spectral refactorisation of rho_t (qst_refactor;
  *          the spectral step with eta_rho = 0), then P_tau; one proposal.
- * Step sizes (slots 0, 1): eta = eta0 * eta_ratio^j, j = 0 .. n_eta-1, tried
+ *   slot 3 (T_rho): the spectral step of Sec. III-C with eta_rho from the step
+ *          grid: Ritz pairs of S_t = rho_t + eta G_t (Eqs. density-proposal,
+ *          density-product, ritz-pairs) from a block Krylov space started at
+ *          the atoms (blocks of K vectors, one adjoint per block, full
+ *          reorthogonalisation, at most n_krylov vectors), then the candidates
+ *          P_tau(proj_Delta(lambda_1..s), Phi_s), s = 1..min(K, m), scored by
+ *          Q_t (Eq. proximal-surrogate, evaluated through the Ritz values) and
+ *          the best one proposed (Eq. spectral-selection).  Needs K <= 16 and
+ *          n <= 16.
+ * Step sizes (slots 0, 1, 3): eta = eta0 * eta_ratio^j, j = 0 .. n_eta-1, tried
  * from largest to smallest; the first proposal with
  * J(X~) <= J_t - tau_acc (Eq. state-acceptance-rule) is kept, where
  * J = L_eps + mu R (Eq. fixed-rank-objective).  Defaults (Table I): mu = 1e-3,
@@ -243,6 +252,7 @@ qst_status qst_refactor(qst_plan plan, float *psi, float *w, double tau,
 typedef struct qst_step_params {
     double mu, tau, tau_acc, eta0, eta_ratio;
     int n_eta;
+    int n_krylov;  /* Krylov vectors of the spectral step (Table I: at most 30; default 30) */
 } qst_step_params;
 void qst_step_params_default(qst_step_params *sp);
 qst_status qst_step(qst_plan plan, int slot, int r, float *psi, float *w,

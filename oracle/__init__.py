@@ -240,7 +240,7 @@ def _orth_block(W, drop, scale):
     return (V[:, keep] / np.sqrt(lam[keep])[None, :]).T @ W
 
 
-def krylov_ritz(n, data, psi, w, c_obs, eta, n_krylov=32, drop=1e-10, B=None):
+def krylov_ritz(n, data, psi, w, c_obs, eta, n_krylov=30, drop=1e-10, B=None):
     """Ritz pairs of S = Psi diag(w) Psi^* + eta G (Eqs. density-proposal,
     density-product, ritz-pairs) from a block Krylov space started at the atoms
     (the block of K vectors; one product with G per block, as the adjoint gives):
@@ -303,7 +303,7 @@ def spectral_candidates(lam, eta, mu, tau, L):
 
 
 def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, eta0=1.0, eta_ratio=0.5,
-         n_eta=11, n_krylov=32):
+         n_eta=11, n_krylov=30):
     """One slot of Algorithm 1 with the step grid of Sec. IV (eta = eta0 * eta_ratio^j,
     j = 0..n_eta-1, largest first; the first accepted proposal is kept) and the
     acceptance rule J(X~) <= J_t - tau_acc (Eq. state-acceptance-rule).

@@ -991,6 +991,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 }
 
 #include "qst_update.cuh"
+#include "qst_spectral.cuh"
 #include "qst_wide.cuh"
 #include "qst_fixed.cuh"
 #include "qst_iterate.cuh"
@@ -1043,6 +1044,12 @@ struct qst_plan_s {
     double *step_loss = nullptr;   // [1]
     int *step_kout = nullptr;      // [1]
     int *status = nullptr;
+    // spectral step (block Krylov): basis, S times basis, work block, small matrices
+    float2 *lz_Q = nullptr, *lz_SQ = nullptr, *lz_W = nullptr;
+    double2 *lz_C = nullptr, *lz_P = nullptr, *lz_G = nullptr, *lz_Tm = nullptr, *lz_T = nullptr, *lz_Y = nullptr,
+            *lz_Tc = nullptr;
+    double *lz_lam = nullptr;
+    int *lz_int = nullptr;  // [0] kept count, [1] selected s
     // qst_iterate: device state, trial likelihood ratio, captured graph
     IterState *it_state = nullptr;
     float *it_c = nullptr;
@@ -1402,6 +1409,21 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc) rc = dalloc(p, &p->step_m1, K);
     if (!rc) rc = dalloc(p, &p->step_loss, 1);
     if (!rc) rc = dalloc(p, &p->step_kout, 1);
+    if (!rc && !wide && K <= kRefacMax / 2) {  // the spectral step needs >= 2 Krylov blocks
+        const size_t nv = (size_t)(kKrylovMax + K);
+        rc = dalloc(p, &p->lz_Q, nv * D);
+        if (!rc) rc = dalloc(p, &p->lz_SQ, nv * D);
+        if (!rc) rc = dalloc(p, &p->lz_W, (size_t)K * D);
+        if (!rc) rc = dalloc(p, &p->lz_C, nv * kKrylovMax);
+        if (!rc) rc = dalloc(p, &p->lz_P, (size_t)K * K);
+        if (!rc) rc = dalloc(p, &p->lz_G, (size_t)K * K);
+        if (!rc) rc = dalloc(p, &p->lz_Tm, (size_t)K * K);
+        if (!rc) rc = dalloc(p, &p->lz_T, (size_t)kKrylovMax * kKrylovMax);
+        if (!rc) rc = dalloc(p, &p->lz_Y, (size_t)kKrylovMax * kKrylovMax);
+        if (!rc) rc = dalloc(p, &p->lz_Tc, (size_t)kKrylovMax * K);
+        if (!rc) rc = dalloc(p, &p->lz_lam, kKrylovMax);
+        if (!rc) rc = dalloc(p, &p->lz_int, 2);
+    }
     if (!rc) rc = dalloc(p, &p->it_state, 1);
     if (!rc && cudaMemset(p->it_state, 0, sizeof(IterState)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) rc = dalloc(p, &p->it_c, nnz);
@@ -1455,6 +1477,10 @@ qst_status qst_plan_destroy(qst_plan p) {
     cudaFree(p->h_dev);
     cudaFree(p->it_state);
     cudaFree(p->it_c);
+    for (void *q : {(void *)p->lz_Q, (void *)p->lz_SQ, (void *)p->lz_W, (void *)p->lz_C, (void *)p->lz_P,
+                    (void *)p->lz_G, (void *)p->lz_Tm, (void *)p->lz_T, (void *)p->lz_Y, (void *)p->lz_Tc,
+                    (void *)p->lz_lam, (void *)p->lz_int})
+        cudaFree(q);
     if (p->it_exec) cudaGraphExecDestroy(p->it_exec);
     if (p->it_cap) cudaStreamDestroy(p->it_cap);
     for (auto &tl : p->pending) {
@@ -1744,6 +1770,110 @@ qst_status qst_simplex_project(const double *v, int K, double tau, double *beta,
     return cudaGetLastError() == cudaSuccess ? QST_OK : QST_ERR_CUDA;
 }
 
+}  // extern "C"
+
+namespace {
+// The spectral step's proposal for one eta (Sec. III-C): block Krylov basis of
+// S = Psi diag(w) Psi^* + eta G started at the atoms, Rayleigh-Ritz, candidates,
+// selection.  Writes the proposal's atoms (K rows; zero beyond the kept count)
+// and weights.  G uses the likelihood ratio of the current state in
+// p->step_c.  Synchronises to read the size of each orthonormalised block.
+qst_status spectral_candidate(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr,
+                              const uint32_t *outcome, double eta, const qst_step_params &sp, float2 *trial,
+                              float *tw, cudaStream_t st) {
+    const int K = p->K;
+    const int64_t D = (int64_t)1 << p->n;
+    const size_t vb = sizeof(float2) * (size_t)D;
+    const float2 *ps = reinterpret_cast<const float2 *>(psi);
+    const int cgrid = (int)((D + 255) / 256 < 148 * 8 ? (D + 255) / 256 : 148 * 8);
+    constexpr double kDrop = 1e-10;
+    qst_status rc = QST_OK;
+    auto read_int = [&](int *h) -> qst_status {
+        if (cudaMemcpyAsync(h, p->lz_int, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return QST_ERR_CUDA;
+        return QST_OK;
+    };
+    // W (kb rows) -> orthonormal rows in place (kept first); P: its Gram matrix before projections
+    auto orth = [&](int kb, const double2 *P, int *kept) -> qst_status {
+        qst_status r2 = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_xgram<<<kb * kb, 256, 0, st>>>(p->lz_W, kb, p->lz_W, kb, D, p->lz_G, kb);
+        });
+        if (!r2) r2 = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_orth_coef<<<1, kRefacMax, 0, st>>>(p->lz_G, P, kb, kDrop, p->lz_Tm, p->lz_int);
+        });
+        if (!r2) r2 = launch(p, QST_KERNEL_STEP, st, [&] { k_combine<<<cgrid, 256, 0, st>>>(p->lz_W, kb, D, p->lz_Tm); });
+        if (!r2) r2 = read_int(kept);
+        return r2;
+    };
+    // block 0: the atoms
+    if (cudaMemcpyAsync(p->lz_W, psi, vb * K, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return QST_ERR_CUDA;
+    rc = launch(p, QST_KERNEL_STEP, st, [&] { k_xgram<<<K * K, 256, 0, st>>>(ps, K, ps, K, D, p->lz_P, K); });
+    int kb = 0;
+    if (!rc) rc = orth(K, p->lz_P, &kb);
+    if (rc) return rc;
+    int m = 0, mb = 0;
+    if (kb > 0 && cudaMemcpyAsync(p->lz_Q, p->lz_W, vb * kb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return QST_ERR_CUDA;
+    m = kb;
+    while (kb > 0) {
+        // SQ_block = eta G Q_block + Psi diag(w) (Psi^* Q_block); the adjoint takes K rows, zero beyond kb
+        float2 *qb = p->lz_Q + (size_t)mb * D, *sq = p->lz_SQ + (size_t)mb * D;
+        if (kb < K && cudaMemsetAsync(p->lz_Q + (size_t)m * D, 0, vb * (K - kb), st) != cudaSuccess) return QST_ERR_CUDA;
+        rc = adjoint_core(p, reinterpret_cast<const float *>(qb), p->step_m1, row_ptr, outcome, p->step_c,
+                          reinterpret_cast<float *>(sq), nullptr, st);
+        if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_xgram<<<K * kb, 256, 0, st>>>(ps, K, qb, kb, D, p->lz_C, kb);
+        });
+        if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_lincomb<<<cgrid, 256, 0, st>>>(sq, kb, eta, ps, K, p->lz_C, kb, w, 1.0, D);
+        });
+        if (rc) return rc;
+        if (m + K > sp.n_krylov) break;
+        // W = SQ_block minus its components on the basis, twice; then orthonormalise
+        if (cudaMemcpyAsync(p->lz_W, sq, vb * kb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return QST_ERR_CUDA;
+        rc = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_xgram<<<kb * kb, 256, 0, st>>>(p->lz_W, kb, p->lz_W, kb, D, p->lz_P, kb);
+        });
+        for (int pass = 0; pass < 2 && !rc; ++pass) {
+            rc = launch(p, QST_KERNEL_STEP, st, [&] {
+                k_xgram<<<m * kb, 256, 0, st>>>(p->lz_Q, m, p->lz_W, kb, D, p->lz_C, kb);
+            });
+            if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
+                k_lincomb<<<cgrid, 256, 0, st>>>(p->lz_W, kb, 1.0, p->lz_Q, m, p->lz_C, kb, nullptr, -1.0, D);
+            });
+        }
+        int kn = 0;
+        if (!rc) rc = orth(kb, p->lz_P, &kn);
+        if (rc) return rc;
+        if (kn == 0) break;
+        if (cudaMemcpyAsync(p->lz_Q + (size_t)m * D, p->lz_W, vb * kn, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return QST_ERR_CUDA;
+        mb = m;
+        kb = kn;
+        m += kn;
+    }
+    if (m == 0) return QST_ERR_INVALID_ARG;  // every atom is zero
+    // Rayleigh-Ritz and the candidates
+    rc = launch(p, QST_KERNEL_STEP, st, [&] {
+        k_xgram<<<m * m, 256, 0, st>>>(p->lz_Q, m, p->lz_SQ, m, D, p->lz_T, m);
+    });
+    if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] { k_heig<<<1, kRefacMax, 0, st>>>(p->lz_T, m, p->lz_lam, p->lz_Y); });
+    const int L = K < m ? K : m;
+    if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
+        k_spectral_select<<<1, 32, 0, st>>>(p->lz_lam, p->lz_Y, m, L, eta, sp.mu, sp.tau, K, p->lz_Tc, tw, p->lz_int,
+                                            p->lz_int + 1);
+    });
+    if (!rc && cudaMemsetAsync(trial, 0, vb * K, st) != cudaSuccess) rc = QST_ERR_CUDA;
+    if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
+        k_lincomb<<<cgrid, 256, 0, st>>>(trial, K, 0.0, p->lz_Q, m, p->lz_Tc, K, nullptr, 1.0, D);
+    });
+    return rc;
+}
+}  // namespace
+
+extern "C" {
+
 void qst_step_params_default(qst_step_params *sp) {
     if (!sp) return;
     sp->mu = 1e-3;
@@ -1752,18 +1882,20 @@ void qst_step_params_default(qst_step_params *sp) {
     sp->eta0 = 1.0;
     sp->eta_ratio = 0.5;
     sp->n_eta = 11;
+    sp->n_krylov = 30;
 }
 
 qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uint8_t *basis, const int64_t *row_ptr,
                     const uint32_t *outcome, const uint32_t *count, const uint32_t *shots,
                     const qst_step_params *params, double *J_out, int *accepted, double *eta_used, void *stream) {
     if (!p || !psi || !w || !basis || !row_ptr || !shots || !J_out || !accepted || !eta_used) return QST_ERR_INVALID_ARG;
-    if (slot < 0 || slot > 2 || (slot == 0 && (r < 0 || r >= p->K))) return QST_ERR_INVALID_ARG;
-    if (p->K > kProjMax || (slot == 2 && !p->refac_C)) return QST_ERR_UNSUPPORTED;
+    if (slot < 0 || slot > 3 || (slot == 0 && (r < 0 || r >= p->K))) return QST_ERR_INVALID_ARG;
+    if (p->K > kProjMax || (slot == 2 && !p->refac_C) || (slot == 3 && !p->lz_Q)) return QST_ERR_UNSUPPORTED;
     qst_step_params sp;
     qst_step_params_default(&sp);
     if (params) sp = *params;
     if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0)) return QST_ERR_INVALID_ARG;
+    if (slot == 3 && (sp.n_krylov < 2 * p->K || sp.n_krylov > kKrylovMax)) return QST_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int K = p->K;
     const size_t D = (size_t)1 << p->n;
@@ -1810,6 +1942,27 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
         return QST_OK;
     }
     double eta = sp.eta0;
+    if (slot == 3) {  // spectral step (Sec. III-C) with eta_rho on the step grid
+        for (int j = 0; j < sp.n_eta; ++j, eta *= sp.eta_ratio) {
+            rc = spectral_candidate(p, psi, w, row_ptr, outcome, eta, sp, p->step_trial, p->step_tw, st);
+            if (rc) return rc;
+            double Jt = 0.0;
+            rc = evaluate(trial_psi, p->step_tw, nullptr, &Jt);
+            if (rc) return rc;
+            if (Jt <= J0 - sp.tau_acc) {
+                if (cudaMemcpyAsync(psi, trial_psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                    cudaMemcpyAsync(w, p->step_tw, sizeof(float) * K, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    return QST_ERR_CUDA;
+                *J_out = Jt;
+                *accepted = 1;
+                *eta_used = eta;
+                return QST_OK;
+            }
+        }
+        *eta_used = eta / sp.eta_ratio;
+        return QST_OK;
+    }
     if (slot == 0) {  // atom r (Eqs. atom-direction, atom-trial)
         rc = qst_adjoint(p, psi, p->step_m1, basis, row_ptr, outcome, p->step_c,
                          reinterpret_cast<float *>(p->step_grad), nullptr, stream);

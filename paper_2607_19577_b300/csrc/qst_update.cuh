@@ -199,33 +199,14 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// Eigen-decomposition of H = diag(sqrt w) C diag(sqrt w) (complex Hermitian,
-// FP64) by cyclic Jacobi (Golub & Van Loan, Sec. 8.5), one CTA, K <= kRefacMax.
-// Each rotation first removes the phase of H_pq, then applies the real
-// symmetric Jacobi rotation; bounded sweep count.  Then: eigenpairs sorted
-// descending, weights lambda / sum(lambda), P_tau, and the combination matrix
-// T = diag(sqrt w) V_kept diag(1/sqrt lambda) (K x K, zero columns beyond K').
-__global__ void __launch_bounds__(kRefacMax) k_eig(const double2 *__restrict__ Cin, const float *__restrict__ w,
-                                                   int K, double tau, double2 *__restrict__ T,
-                                                   float *__restrict__ w_out, int *__restrict__ kout) {
-    __shared__ double2 H[kRefacMax][kRefacMax + 1];
-    __shared__ double2 V[kRefacMax][kRefacMax + 1];
-    __shared__ double lam[kRefacMax], sw[kRefacMax], wt[kRefacMax];
-    __shared__ int ord[kRefacMax], keepj[kRefacMax];
+// Cyclic Jacobi on the Hermitian K x K matrix H (shared, row stride kRefacMax + 1),
+// accumulating the rotations into V (Golub & Van Loan, Sec. 8.5): each rotation
+// first removes the phase of H_pq, then applies the real symmetric Jacobi
+// rotation.  Bounded sweep count; called by all threads of one CTA (>= K).
+__device__ void jacobi_hermitian(double2 (*H)[kRefacMax + 1], double2 (*V)[kRefacMax + 1], int K) {
     __shared__ double2 rot[4];  // (c, s e^{i phi}) pieces of the current rotation
     __shared__ int skip;
-    __shared__ int nk_sm;
     const int t = threadIdx.x;
-    if (t < K) sw[t] = sqrt(fmax((double)w[t], 0.0));
-    __syncthreads();
-    if (t < K) {
-        for (int j = 0; j < K; ++j) {
-            double2 c = (t <= j) ? Cin[(size_t)t * K + j] : cconj(Cin[(size_t)j * K + t]);
-            H[t][j] = make_double2(c.x * sw[t] * sw[j], c.y * sw[t] * sw[j]);
-            V[t][j] = make_double2(t == j ? 1.0 : 0.0, 0.0);
-        }
-    }
-    __syncthreads();
     for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
         // off-diagonal norm vs diagonal: stop when negligible
         if (t == 0) {
@@ -284,6 +265,34 @@ __global__ void __launch_bounds__(kRefacMax) k_eig(const double2 *__restrict__ C
             }
         }
     }
+}
+
+// Eigen-decomposition of H = diag(sqrt w) C diag(sqrt w) (complex Hermitian,
+// FP64) by cyclic Jacobi (Golub & Van Loan, Sec. 8.5), one CTA, K <= kRefacMax.
+// Each rotation first removes the phase of H_pq, then applies the real
+// symmetric Jacobi rotation; bounded sweep count.  Then: eigenpairs sorted
+// descending, weights lambda / sum(lambda), P_tau, and the combination matrix
+// T = diag(sqrt w) V_kept diag(1/sqrt lambda) (K x K, zero columns beyond K').
+__global__ void __launch_bounds__(kRefacMax) k_eig(const double2 *__restrict__ Cin, const float *__restrict__ w,
+                                                   int K, double tau, double2 *__restrict__ T,
+                                                   float *__restrict__ w_out, int *__restrict__ kout) {
+    __shared__ double2 H[kRefacMax][kRefacMax + 1];
+    __shared__ double2 V[kRefacMax][kRefacMax + 1];
+    __shared__ double lam[kRefacMax], sw[kRefacMax], wt[kRefacMax];
+    __shared__ int ord[kRefacMax], keepj[kRefacMax];
+    __shared__ int nk_sm;
+    const int t = threadIdx.x;
+    if (t < K) sw[t] = sqrt(fmax((double)w[t], 0.0));
+    __syncthreads();
+    if (t < K) {
+        for (int j = 0; j < K; ++j) {
+            double2 c = (t <= j) ? Cin[(size_t)t * K + j] : cconj(Cin[(size_t)j * K + t]);
+            H[t][j] = make_double2(c.x * sw[t] * sw[j], c.y * sw[t] * sw[j]);
+            V[t][j] = make_double2(t == j ? 1.0 : 0.0, 0.0);
+        }
+    }
+    __syncthreads();
+    jacobi_hermitian(H, V, K);
     if (t == 0) {
         double tot = 0.0;
         for (int j = 0; j < K; ++j) {

@@ -43,7 +43,8 @@ class _Params(ctypes.Structure):
 
 class _StepParams(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("tau", ctypes.c_double), ("tau_acc", ctypes.c_double),
-                ("eta0", ctypes.c_double), ("eta_ratio", ctypes.c_double), ("n_eta", ctypes.c_int)]
+                ("eta0", ctypes.c_double), ("eta_ratio", ctypes.c_double), ("n_eta", ctypes.c_int),
+                ("n_krylov", ctypes.c_int)]
 
 
 class _IterParams(ctypes.Structure):
@@ -275,7 +276,8 @@ class Plan:
         return k_out
 
     def step(self, slot, r, psi, w, d: Data, **params):
-        """qst_step: one slot of Algorithm 1 (0 = atom r, 1 = coefficients, 2 = refactor),
+        """qst_step: one slot of Algorithm 1 (0 = atom r, 1 = coefficients, 2 = refactor,
+        3 = spectral step with Lanczos Ritz pairs),
         in place on psi and w.  Returns (J, accepted, eta_used)."""
         _need(psi, torch.complex64, (self.K, self.D), "psi")
         _need(w, torch.float32, (self.K,), "w")

@@ -176,3 +176,35 @@ def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref):
     assert torch.equal(dp, hp) and torch.equal(dw, hw)
     assert sum(acc_h) > 0
     plan.close()
+
+
+@pytest.mark.parametrize("name,K,seed", [("n4_all81", 4, 3), ("n8_m40_k4", 4, 5), ("n10_m60_k8", 8, 7)])
+def test_spectral_step_matches_oracle(name, K, seed):
+    """qst_step slot 3 (Sec. III-C: block Krylov Ritz pairs of S = rho + eta G, the
+    scored candidates, the best one, acceptance over the step grid) against the
+    oracle's slot 3: same acceptance and step, J within 1e-5, and the same state at
+    the rho level.  At n = 4 the Krylov space spans C^16 (exact eigenpairs)."""
+    inst = synth.make_instance(name, seed=seed, K=K)
+    n = inst.n
+    psi0 = inst.psi.astype(np.complex128)
+    psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
+    w0 = inst.w.astype(np.float64)
+    data = dict(basis=inst.basis, row_ptr=inst.row_ptr, outcome=inst.outcome, count=inst.count, shots=inst.shots)
+    plan = qst.Plan(n, inst.M, K, inst.nnz)
+    d = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    tp = torch.from_numpy(psi0.astype(np.complex64)).cuda()
+    tw = torch.from_numpy(w0.astype(np.float32)).cuda()
+    J, acc, eta = plan.step(3, 0, tp, tw, d)
+    # the oracle starts from the same (FP32-rounded) state
+    op, ow, oJ, oacc, oeta = oracle.step(n, data, psi0.astype(np.complex64).astype(np.complex128),
+                                         w0.astype(np.float32).astype(np.float64), 3, 0, n_krylov=30)
+    assert acc == oacc and abs(eta - oeta) <= 1e-12 * max(1.0, oeta), (acc, oacc, eta, oeta)
+    assert abs(J - oJ) <= 1e-5 * abs(oJ), (J, oJ)
+    gp = tp.cpu().numpy().astype(np.complex128)
+    gw = tw.cpu().numpy().astype(np.float64)
+    a, b = gw > 0, ow > 0
+    assert a.sum() == b.sum()
+    np.testing.assert_allclose(np.sort(gw[a]), np.sort(ow[b]), atol=2e-5)
+    assert _gram_frob2(gp[a], gw[a], op[b], ow[b]) <= 1e-8
+    np.testing.assert_allclose(gp[a].conj() @ gp[a].T, np.eye(a.sum()), atol=2e-5)
+    plan.close()
