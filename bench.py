@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--chunk-qubits", type=int, default=0)
     ap.add_argument("--max-bin-settings", type=int, default=0)
     ap.add_argument("--autotune", action="store_true", help="time candidate plan layouts first and use the fastest")
+    ap.add_argument("--iterations", type=int, default=10, help="Algorithm 1 iterations timed through qst_iterate")
+    ap.add_argument("--no-iterations", action="store_true")
     ap.add_argument("--per-setting-rounds", action="store_true",
                     help="choose each setting's rounds (instead of fixed qubit groups for 12-qubit chunks)")
     return ap.parse_args()
@@ -323,6 +325,30 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * t_e2e / args.steps}
 
+    # Algorithm 1 iterations on the device (qst_iterate: one CUDA graph, atom /
+    # coefficient slots of the Table I schedule), timed with CUDA events
+    algo = None
+    if not args.no_iterations:
+        it_T = args.iterations
+        ip_psi, ip_w = psi.clone(), w.clone()
+        Jh, acc = plan.iterate(it_T, 0, ip_psi, ip_w, data)  # capture + first run (untimed)
+        ip_psi.copy_(psi)
+        ip_w.copy_(w)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.iterate(it_T, 0, ip_psi, ip_w, data, J_hist=Jh, accepted=acc)  # graph replay
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plan.check()
+        ms_it, _ = replicas.aggregate(e0.elapsed_time(e1), 0, dist, device="cuda")
+        jh = Jh.cpu().numpy()
+        algo = {"s_per_iteration": ms_it / 1e3 / it_T, "iterations": it_T, "accepted": int(acc.sum().item()),
+                "J_first": float(jh[0]), "J_last": float(jh[-1]),
+                "how": "qst_iterate replay (one CUDA graph), Table I schedule (T_alpha = 5), step grid 2^-j, "
+                       "from the bench state"}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         done, t = cpu_oracle_rate(inst, args.cpu_seconds)
@@ -343,6 +369,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "algorithm1": algo,
                 "gpu_launches": launches, "kernels": kern, "wall_ms_per_step": 1e3 * t_wall / args.steps,
                 "workspace_bytes": plan.workspace_bytes()}
         print(json.dumps(line), flush=True)
