@@ -17,7 +17,8 @@ FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std
 
 
 def build(force: bool = False, verbose: bool = False) -> Path:
-    stale = (not LIB.exists() or LIB.stat().st_mtime < max(SRC.stat().st_mtime, HDR.stat().st_mtime))
+    deps = [SRC, HDR, *sorted((PKG / "csrc").glob("*.cuh"))]
+    stale = not LIB.exists() or LIB.stat().st_mtime < max(d.stat().st_mtime for d in deps)
     if force or stale:
         tmp = LIB.with_suffix(".so.tmp%d" % os.getpid())
         cmd = [NVCC, *FLAGS, *(["-Xptxas", "-v"] if verbose else []), "-o", str(tmp), str(SRC)]

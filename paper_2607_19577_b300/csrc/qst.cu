@@ -1053,7 +1053,7 @@ struct qst_plan_s {
     // qst_iterate: device state, trial likelihood ratio, captured graph
     IterState *it_state = nullptr;
     float *it_c = nullptr;
-    cudaStream_t it_cap = nullptr;
+    cudaStream_t it_cap = nullptr, it_body = nullptr;  // capture streams (main graph, conditional bodies)
     cudaGraphExec_t it_exec = nullptr;
     std::vector<double> it_key;
     int64_t it_launches = 0;
@@ -1483,6 +1483,7 @@ qst_status qst_plan_destroy(qst_plan p) {
         cudaFree(q);
     if (p->it_exec) cudaGraphExecDestroy(p->it_exec);
     if (p->it_cap) cudaStreamDestroy(p->it_cap);
+    if (p->it_body) cudaStreamDestroy(p->it_body);
     for (auto &tl : p->pending) {
         cudaEventDestroy(tl.start);
         cudaEventDestroy(tl.stop);
@@ -2036,7 +2037,58 @@ int iter_slot(const qst_iter_params &ip, int64_t t) {
     return 0;
 }
 
+qst_status graph_fail(const char *what, cudaError_t e) {
+    fprintf(stderr, "qst_iterate: %s failed: %s\n", what, cudaGetErrorString(e));
+    return QST_ERR_CUDA;
+}
+// A new condition on the graph being captured on s.  It is 0 at every launch of
+// the graph until a kernel sets it.  A handle serves one conditional node.
+qst_status new_condition(cudaStream_t s, cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusActive) return graph_fail("cudaStreamGetCaptureInfo", e);
+    if ((e = cudaGraphConditionalHandleCreate(h, g, 0u, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return graph_fail("cudaGraphConditionalHandleCreate", e);
+    return QST_OK;
+}
+// Conditional "if" node on the graph being captured on s, gated by `cond`;
+// its body is captured on the plan's body stream, returned in *body_stream.
+qst_status begin_if(qst_plan p, cudaStream_t s, cudaGraphConditionalHandle cond, cudaStream_t *body_stream) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusActive) return graph_fail("cudaStreamGetCaptureInfo", e);
+    // (the parameter union has no default constructor: zeroed storage instead)
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams *np = reinterpret_cast<cudaGraphNodeParams *>(raw);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = cond;
+    np->conditional.type = cudaGraphCondTypeIf;
+    np->conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, np)) != cudaSuccess) return graph_fail("cudaGraphAddNode", e);
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return graph_fail("cudaStreamUpdateCaptureDependencies", e);
+    if ((e = cudaStreamBeginCaptureToGraph(p->it_body, np->conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return graph_fail("cudaStreamBeginCaptureToGraph", e);
+    *body_stream = p->it_body;
+    return QST_OK;
+}
+qst_status end_if(qst_plan p) {
+    cudaGraph_t body = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->it_body, &body);
+    return e == cudaSuccess ? QST_OK : graph_fail("cudaStreamEndCapture (conditional body)", e);
+}
+
 // The launch sequence of qst_iterate on stream s (captured by the caller).
+// Trial j > 0 of a step grid sits in a conditional node that trial j - 1's
+// acceptance kernel opens only when it rejects: once a trial is accepted the
+// remaining trials are not launched at all.
 qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, const uint8_t *basis,
                             const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
                             const uint32_t *shots, const qst_iter_params &ip, double *J_hist, int *acc_hist,
@@ -2049,6 +2101,36 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
     float *grad = reinterpret_cast<float *>(p->step_grad);
     const int *done = &p->it_state->done;
     const int *rdev = &p->it_state->r;
+    // One step grid: trial j proposes (psi_t, w_t) with `propose(stream, eta)`,
+    // evaluates J there and applies the acceptance rule.
+    auto step_grid = [&](const float *psi_t, const float *w_t, auto &&propose) -> qst_status {
+        cudaGraphConditionalHandle cur = 0, next = 0;
+        double eta = sp.eta0;
+        qst_status rc = QST_OK;
+        for (int j = 0; j < sp.n_eta && !rc; ++j, eta *= sp.eta_ratio) {
+            const int has_next = j + 1 < sp.n_eta;
+            if (has_next) rc = new_condition(s, &next);
+            cudaStream_t ts = s;
+            bool opened = false;
+            if (!rc && j > 0) {
+                rc = begin_if(p, s, cur, &ts);
+                opened = !rc;
+            }
+            if (!rc) rc = propose(ts, eta);
+            if (!rc) rc = forward_core(p, psi_t, w_t, row_ptr, outcome, count, shots, nullptr, p->it_c, p->step_loss,
+                                       nullptr, done, ts);
+            if (!rc) rc = launch(p, QST_KERNEL_STEP, ts, [&] {
+                k_iter_accept<<<1, 32, 0, ts>>>(p->it_state, p->step_loss, w_t, K, sp.mu, sp.tau_acc, j, eta, has_next,
+                                                next);
+            });
+            if (opened) {
+                const qst_status re = end_if(p);
+                if (!rc) rc = re;
+            }
+            cur = next;
+        }
+        return rc;
+    };
     qst_status rc = prepare(p, basis, row_ptr, outcome, shots, s);
     if (!rc) rc = forward_core(p, psi, w, row_ptr, outcome, count, shots, nullptr, p->step_c, p->step_loss, nullptr,
                                nullptr, s);
@@ -2060,33 +2142,22 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
         const int slot = iter_slot(ip, (int64_t)t0 + i);
         rc = launch(p, QST_KERNEL_STEP, s, [&] { k_iter_begin<<<1, 32, 0, s>>>(p->it_state, w, K, slot); });
         if (rc) break;
-        double eta = sp.eta0;
         if (slot == 0) {  // atom r_t along its projected direction (Eqs. atom-direction, atom-trial)
             rc = adjoint_core(p, psi, p->step_m1, row_ptr, outcome, p->step_c, grad, nullptr, s);
             if (!rc && cudaMemcpyAsync(trial, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
                 rc = QST_ERR_CUDA;
-            for (int j = 0; j < sp.n_eta && !rc; ++j, eta *= sp.eta_ratio) {
-                rc = launch(p, QST_KERNEL_STEP, s, [&] {
-                    k_atom_trial<<<1, 1024, 0, s>>>(ps, p->step_grad, w, rdev, 0, eta, D, p->step_trial, done);
+            if (!rc) rc = step_grid(trial, w, [&](cudaStream_t ts, double eta) {
+                return launch(p, QST_KERNEL_STEP, ts, [&] {
+                    k_atom_trial<<<1, 1024, 0, ts>>>(ps, p->step_grad, w, rdev, 0, eta, D, p->step_trial, done);
                 });
-                if (!rc) rc = forward_core(p, trial, w, row_ptr, outcome, count, shots, nullptr, p->it_c, p->step_loss,
-                                           nullptr, done, s);
-                if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
-                    k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, w, K, sp.mu, sp.tau_acc, j, eta);
-                });
-            }
+            });
         } else if (slot == 1) {  // coefficients (Eq. coefficient-update, then P_tau)
             rc = adjoint_core(p, psi, w, row_ptr, outcome, p->step_c, grad, p->step_gw, s);
-            for (int j = 0; j < sp.n_eta && !rc; ++j, eta *= sp.eta_ratio) {
-                rc = launch(p, QST_KERNEL_STEP, s, [&] {
-                    k_coeff_trial<<<1, kProjMax, 0, s>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw, done);
+            if (!rc) rc = step_grid(psi, p->step_tw, [&](cudaStream_t ts, double eta) {
+                return launch(p, QST_KERNEL_STEP, ts, [&] {
+                    k_coeff_trial<<<1, kProjMax, 0, ts>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw, done);
                 });
-                if (!rc) rc = forward_core(p, psi, p->step_tw, row_ptr, outcome, count, shots, nullptr, p->it_c,
-                                           p->step_loss, nullptr, done, s);
-                if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
-                    k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, p->step_tw, K, sp.mu, sp.tau_acc, j, eta);
-                });
-            }
+            });
         } else {  // exact spectral refactorisation (eta_rho = 0)
             if (cudaMemcpyAsync(trial, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
                 cudaMemcpyAsync(p->step_tw, w, sizeof(float) * K, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -2095,7 +2166,7 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
             if (!rc) rc = forward_core(p, trial, p->step_tw, row_ptr, outcome, count, shots, nullptr, p->it_c,
                                        p->step_loss, nullptr, nullptr, s);
             if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
-                k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, p->step_tw, K, sp.mu, sp.tau_acc, 0, 0.0);
+                k_iter_accept<<<1, 32, 0, s>>>(p->it_state, p->step_loss, p->step_tw, K, sp.mu, sp.tau_acc, 0, 0.0, 0, 0);
             });
         }
         if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
@@ -2143,6 +2214,8 @@ qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const ui
         }
         if (!p->it_cap && cudaStreamCreateWithFlags(&p->it_cap, cudaStreamNonBlocking) != cudaSuccess)
             return QST_ERR_CUDA;
+        if (!p->it_body && cudaStreamCreateWithFlags(&p->it_body, cudaStreamNonBlocking) != cudaSuccess)
+            return QST_ERR_CUDA;
         const bool timing = p->timing;
         const int64_t before = p->total_launches;
         p->timing = false;  // no event records inside the graph
@@ -2159,17 +2232,18 @@ qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const ui
         p->total_launches = before;
         if (rc || ce != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
-            return rc ? rc : QST_ERR_CUDA;
+            return rc ? rc : graph_fail("cudaStreamEndCapture", ce);
         }
         const cudaError_t ie = cudaGraphInstantiate(&p->it_exec, g, 0);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) {
             p->it_exec = nullptr;
-            return QST_ERR_CUDA;
+            return graph_fail("cudaGraphInstantiate", ie);
         }
         p->it_key = key;
     }
-    if (cudaGraphLaunch(p->it_exec, st) != cudaSuccess) return QST_ERR_CUDA;
+    const cudaError_t le = cudaGraphLaunch(p->it_exec, st);
+    if (le != cudaSuccess) return graph_fail("cudaGraphLaunch", le);
     p->total_launches += p->it_launches;
     return QST_OK;
 }

@@ -54,8 +54,12 @@ __global__ void k_iter_begin(IterState *s, const float *w, int K, int slot) {
 
 // Acceptance of trial j (Sec. III-D): J~ = L~ + mu R~ <= J - tau_acc, where
 // R~ counts the trial's atoms with w > 0.  The first accepted trial wins.
+// Trial j + 1 sits in a conditional graph node whose condition defaults to 0
+// at every graph launch; only a rejected trial j opens it (has_next = 0 for
+// the last trial of a grid).  A trial that did not run opens nothing, so once
+// a trial is accepted, or the slot has nothing to do, no later trial launches.
 __global__ void k_iter_accept(IterState *s, const double *loss, const float *w_trial, int K, double mu,
-                              double tau_acc, int j, double eta) {
+                              double tau_acc, int j, double eta, int has_next, cudaGraphConditionalHandle next) {
     if (threadIdx.x | blockIdx.x) return;
     if (s->done) return;
     const double Jt = iter_J(*loss, mu, iter_active(w_trial, K));
@@ -64,6 +68,8 @@ __global__ void k_iter_accept(IterState *s, const double *loss, const float *w_t
         s->acc = j;
         s->J = Jt;
         s->eta = eta;
+    } else if (has_next) {
+        cudaGraphSetConditional(next, 1u);
     }
 }
 
