@@ -51,8 +51,9 @@ def parse_args():
     ap.add_argument("--autotune", action="store_true", help="time candidate plan layouts first and use the fastest")
     ap.add_argument("--iterations", type=int, default=10, help="Algorithm 1 iterations timed through qst_iterate")
     ap.add_argument("--no-iterations", action="store_true")
-    ap.add_argument("--per-setting-rounds", action="store_true",
-                    help="choose each setting's rounds (instead of fixed qubit groups for 12-qubit chunks)")
+    ap.add_argument("--fixed-rounds", type=int, default=2, choices=[0, 1, 2],
+                    help="12-qubit chunk kernels: 2 = two 6-qubit rounds, 1 = three 4-qubit rounds, "
+                         "0 = rounds chosen per setting")
     return ap.parse_args()
 
 
@@ -209,10 +210,10 @@ def run_ours(args):
         best, table = qst.autotune(psi, w, data, eps=inst.eps)
         args.reg_bits, args.chunk_qubits, args.max_bin_settings = (best["reg_bits"], best["chunk_qubits"],
                                                                     best["max_bin_settings"])
-        args.per_setting_rounds = not best["fixed_rounds"]
+        args.fixed_rounds = best["fixed_rounds"]
         tuned = [{"params": p, "ms": t} for p, t in table]
     plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
-                    max_bin_settings=args.max_bin_settings, fixed_rounds=not args.per_setting_rounds)
+                    max_bin_settings=args.max_bin_settings, fixed_rounds=args.fixed_rounds)
     p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
     c_obs = torch.empty_like(p_obs)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -276,6 +277,7 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_alu = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # TFLOP/s, 1 per lane-op
     achieved = adj_ops / (adj_ms / 1e3) / 1e12
+    adj_kernel = {2: "k_adjoint_2r", 1: "k_adjoint_fx"}.get(geo["fixed_rounds"], "k_adjoint")
     traffic = None
     prof = os.path.join(ROOT, "profiles", "adjoint_traffic.json")
     if os.path.exists(prof):
@@ -283,13 +285,13 @@ def run_ours(args):
             rec = json.load(open(prof))
             # counters only count for the kernel source they were taken on
             if (rec.get("source_sha256") == kernel_source_hash() and rec.get("workload") == args.workload
-                    and rec.get("kernel") == ("k_adjoint_fx" if geo["fixed_rounds"] else "k_adjoint")):
+                    and rec.get("kernel") == adj_kernel):
                 traffic = rec.get("bytes_per_launch")
         except Exception:
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                 "frac": achieved / peak_alu, "traffic": traffic,
-                "kernel": "k_adjoint_fx" if geo["fixed_rounds"] else "k_adjoint",
+                "kernel": adj_kernel,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                "(max SM clock of MEASURED_PEAKS.json)",
                 "ops_per_launch": adj_ops, "ms_per_launch": adj_ms,

@@ -60,9 +60,12 @@ typedef struct qst_params {
     int max_bin_settings; /* cap on settings per work bin; 0 = auto */
     int validate;         /* 1 = check basis and CSR on the device (default 1) */
     int reg_bits;         /* amplitudes per thread per round = 2^reg_bits: 4 or 5; 0 = auto */
-    int fixed_rounds;     /* 1 = 12-qubit chunks with 16 amplitudes per thread run three rounds on
-                             fixed qubit groups (compile-time shared-memory offsets, warp-local
-                             middle exchange); 0 = rounds chosen per setting (default 1) */
+    int fixed_rounds;     /* 12-qubit chunks only.  2 = two rounds of six qubits, 64 amplitudes per
+                             thread, two atoms per CTA (one shared-memory exchange per setting in
+                             the forward, two in the adjoint); 1 = three rounds of four qubits on
+                             fixed qubit groups, 16 amplitudes per thread (compile-time
+                             shared-memory offsets, warp-local middle exchange); 0 = rounds chosen
+                             per setting.  Other values: QST_ERR_INVALID_ARG.  Default 2. */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;
@@ -90,8 +93,9 @@ qst_status qst_plan_workspace_bytes(qst_plan plan, int64_t *bytes);
 
 /* The plan's chunk geometry: qubits transformed on-chip per work unit, high
  * qubits applied outside the chunk (by setting bins, or by butterfly passes
- * for n = 17..20), and whether the fixed-group round kernels run (1) or the
- * per-setting ones (0).  Any output pointer may be NULL.  Host only. */
+ * for n = 17..20), and which chunk kernels run: 2 = two 6-qubit rounds,
+ * 1 = three fixed 4-qubit rounds, 0 = rounds chosen per setting.  Any output
+ * pointer may be NULL.  Host only. */
 qst_status qst_plan_geometry(qst_plan plan, int *chunk_qubits, int *high_qubits, int *fixed_rounds);
 
 /*

@@ -994,6 +994,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_spectral.cuh"
 #include "qst_wide.cuh"
 #include "qst_fixed.cuh"
+#include "qst_tworound.cuh"
 #include "qst_iterate.cuh"
 
 // ----------------------------------------------------------------- host side
@@ -1015,6 +1016,7 @@ struct qst_plan_s {
     int n = 0, M = 0, K = 0, c = 0, r = 0, A = 0, T = 0, smax = 0, nb_max = 0, B = 0;
     bool wide = false;       // n = 17..20: high bits by butterfly passes, groups of wide_G settings
     bool fx = false;         // 12-qubit chunks with fixed-position rounds (k_forward_fx / k_adjoint_fx)
+    bool fx2 = false;        // 12-qubit chunks in two 6-bit rounds, two atoms per CTA (k_forward_2r / k_adjoint_2r)
     int wide_G = 0;
     float2 *wide_T = nullptr;    // [wide_G][K][D] intermediate (also the z buffer)
     double2 *wide_acc = nullptr; // [K][D] FP64 accumulator of G psi
@@ -1165,8 +1167,15 @@ void with_geo(int c, int ra, Fn &&fn) {
     }
 }
 
-// The plan's forward / adjoint chunk kernel over `grid` work units.
-void launch_forward_units(qst_plan p, const FwdArgs &a, int grid, cudaStream_t st) {
+// The plan's forward / adjoint chunk kernel over `units` work units per atom
+// (bins x high patterns): one CTA per unit and atom, or per unit and atom
+// pair for the two-round kernels.
+void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t st) {
+    if (p->fx2) {
+        k_forward_2r<<<units * ((p->K + 1) / 2), k2T, k2_smem(false).total, st>>>(a);
+        return;
+    }
+    const int grid = units * p->K;
     if (p->fx) {
         k_forward_fx<<<grid, kFxT, fx_smem(false).total, st>>>(a);
         return;
@@ -1176,7 +1185,12 @@ void launch_forward_units(qst_plan p, const FwdArgs &a, int grid, cudaStream_t s
         k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
     });
 }
-void launch_adjoint_units(qst_plan p, const AdjArgs &a, int grid, cudaStream_t st) {
+void launch_adjoint_units(qst_plan p, const AdjArgs &a, int units, cudaStream_t st) {
+    if (p->fx2) {
+        k_adjoint_2r<<<units * ((p->K + 1) / 2), k2T, k2_smem(true).total, st>>>(a);
+        return;
+    }
+    const int grid = units * p->K;
     if (p->fx) {
         k_adjoint_fx<<<grid, kFxT, fx_smem(true).total, st>>>(a);
         return;
@@ -1238,9 +1252,9 @@ qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.n = p->n;
         a.r = p->r;
         a.K = p->K;
-        const int grid = (G << p->r) * p->K;
+        const int units = G << p->r;
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
-            launch_forward_units(p, a, grid, st);
+            launch_forward_units(p, a, units, st);
         });
         if (rc) return rc;
     }
@@ -1277,9 +1291,9 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.n = p->n;
         a.r = p->r;
         a.K = p->K;
-        const int grid = (G << p->r) * p->K;
+        const int units = G << p->r;
         rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
-            launch_adjoint_units(p, a, grid, st);
+            launch_adjoint_units(p, a, units, st);
         });
         if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] {
             k_high_inv_acc<<<dim3(tiles, p->K), 256, 0, st>>>(p->wide_T, p->plans, g0, G, p->K, p->c, p->wide_acc);
@@ -1311,7 +1325,7 @@ void qst_params_default(qst_params *p) {
     p->max_bin_settings = 0;
     p->validate = 1;
     p->reg_bits = 0;
-    p->fixed_rounds = 1;
+    p->fixed_rounds = 2;
 }
 
 const char *qst_status_string(qst_status s) {
@@ -1362,7 +1376,12 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
-    p->fx = c == 12 && p->A == 4 && prm.fixed_rounds != 0;
+    if (prm.fixed_rounds < 0 || prm.fixed_rounds > 2) {
+        delete p;
+        return QST_ERR_INVALID_ARG;
+    }
+    p->fx2 = c == 12 && prm.fixed_rounds == 2;
+    p->fx = c == 12 && p->A == 4 && prm.fixed_rounds == 1;
     p->B = prm.norm_settings ? prm.norm_settings : M;
     cudaGetDevice(&p->device);
     int sms = 148;
@@ -1439,6 +1458,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         if (p->fx) {
             cudaFuncSetAttribute(k_forward_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(false).total);
             cudaFuncSetAttribute(k_adjoint_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
+        }
+        if (p->fx2) {
+            cudaFuncSetAttribute(k_forward_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(false).total);
+            cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(true).total);
         }
         if (cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
     }
@@ -1517,7 +1540,7 @@ qst_status qst_plan_geometry(qst_plan p, int *chunk_qubits, int *high_qubits, in
     if (!p) return QST_ERR_INVALID_ARG;
     if (chunk_qubits) *chunk_qubits = p->c;
     if (high_qubits) *high_qubits = p->r;
-    if (fixed_rounds) *fixed_rounds = p->fx ? 1 : 0;
+    if (fixed_rounds) *fixed_rounds = p->fx2 ? 2 : (p->fx ? 1 : 0);
     return QST_OK;
 }
 
@@ -1569,10 +1592,10 @@ qst_status forward_core(qst_plan p, const float *psi, const float *w, const int6
     a.K = p->K;
     a.src_bin_stride = 0;
     a.skip = skip;
-    const int grid = (p->nb_max << p->r) * p->K;
+    const int units = p->nb_max << p->r;
     if (!p->wide) {
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
-            launch_forward_units(p, a, grid, st);
+            launch_forward_units(p, a, units, st);
         });
         if (rc) return rc;
     }
@@ -1634,9 +1657,9 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
         const float invBw = 1.0f / (float)p->B;
         return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w); });
     }
-    const int grid = (p->nb_max << p->r) * p->K;
+    const int units = p->nb_max << p->r;
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
-        launch_adjoint_units(p, a, grid, st);
+        launch_adjoint_units(p, a, units, st);
     });
     if (rc) return rc;
     const float invB = 1.0f / (float)p->B;

@@ -156,13 +156,15 @@ class Plan:
     """Owns a qst_plan (device workspace for one problem shape)."""
 
     def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
-                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=True):
+                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=2):
         lib = load()
         prm = _Params()
         lib.qst_params_default(ctypes.byref(prm))
         prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
         prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
-        prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(bool(fixed_rounds))
+        # fixed_rounds (12-qubit chunks): 2 = two 6-qubit rounds, 1 = three 4-qubit
+        # rounds, 0 = per-setting rounds (True / False mean 1 / 0)
+        prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(fixed_rounds)
         h = ctypes.c_void_p()
         _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
                "qst_plan_create")
@@ -198,10 +200,11 @@ class Plan:
         return out
 
     def geometry(self):
-        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan."""
+        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan (fixed_rounds:
+        2 = two 6-qubit rounds, 1 = three 4-qubit rounds, 0 = per-setting rounds)."""
         c, r, fx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().qst_plan_geometry(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(fx)), "geometry")
-        return {"chunk_qubits": c.value, "high_qubits": r.value, "fixed_rounds": bool(fx.value)}
+        return {"chunk_qubits": c.value, "high_qubits": r.value, "fixed_rounds": fx.value}
 
     def _data(self, d: Data):
         _need(d.basis, torch.uint8, (self.M, self.n), "basis")
@@ -456,7 +459,7 @@ def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
     (CUDA events on the current stream) over candidate (reg_bits, chunk_qubits,
     max_bin_settings, fixed_rounds) choices: 16 or 32 amplitudes per thread and
     round, the default chunk or one bit smaller, automatic or fixed bin sizes,
-    and fixed-group or per-setting rounds.
+    and two 6-qubit, three 4-qubit or per-setting rounds.
 
     Returns (best params dict, [(params, ms per evaluation), ...])."""
     K, D = psi.shape
@@ -466,7 +469,7 @@ def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
         c0 = n if n <= 12 else (12 if n <= 16 else n - 8)
         chunks = [0] + ([c0 - 1] if 13 <= n <= 16 and c0 - 1 >= n - 4 else [])
         candidates = [dict(reg_bits=rb, chunk_qubits=c, max_bin_settings=sm, fixed_rounds=fx)
-                      for rb in (4, 5) for c in chunks for sm in (0, 32) for fx in (True, False)
+                      for rb in (4, 5) for c in chunks for sm in (0, 32) for fx in (2, 1, 0)
                       if not (fx and rb == 5)]
     results = []
     for prm in candidates:

@@ -240,17 +240,19 @@ def test_autotuner_returns_a_valid_fastest_layout():
     compare(inst, run_gpu(inst, **best), run_oracle(inst))
 
 
-@pytest.mark.parametrize("n,fixed", [(12, True), (12, False), (13, True), (13, False), (16, True), (16, False)])
+@pytest.mark.parametrize("n,fixed", [(n, fx) for n in (12, 13, 16) for fx in (2, 1, 0)])
 def test_parity_fixed_and_per_setting_rounds(n, fixed):
-    """12-qubit chunks run either the fixed-group rounds (bits 8..11, 4..7,
-    0..3) or rounds chosen per setting; both against the oracle, with settings
-    whose whole 4-qubit groups are Z (skipped rounds), all-X, all-Y and random."""
+    """12-qubit chunks run two 6-qubit rounds (bits 6..11, 0..5; two atoms per
+    CTA), three fixed 4-qubit rounds (bits 8..11, 4..7, 0..3) or rounds chosen
+    per setting; all against the oracle, with settings whose whole 4- or
+    6-qubit groups are Z (skipped rounds), all-X, all-Y and random.  K = 3 is
+    odd, so the last two-round CTA has one atom only."""
     rng = synth.rng_for(700 + n)
     M_rand = 14
     special = []
-    for q0 in (0, 4, 8):                      # chunk bits q0..q0+3 all Z, the rest random X/Y
+    for q0, width in ((0, 4), (4, 4), (8, 4), (0, 6), (6, 6)):  # chunk bits q0.. all Z, the rest random X/Y
         row = rng.integers(1, 3, n).astype(np.uint8)
-        for b in range(q0, q0 + 4):
+        for b in range(q0, q0 + width):
             row[n - 1 - b] = 0                # qubit n-1-b carries outcome bit b
         special.append(row)
     special += [np.zeros(n, np.uint8), np.ones(n, np.uint8), np.full(n, 2, np.uint8)]
