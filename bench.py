@@ -51,9 +51,11 @@ def parse_args():
     ap.add_argument("--autotune", action="store_true", help="time candidate plan layouts first and use the fastest")
     ap.add_argument("--iterations", type=int, default=10, help="Algorithm 1 iterations timed through qst_iterate")
     ap.add_argument("--no-iterations", action="store_true")
-    ap.add_argument("--fixed-rounds", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-instance batched evaluation (field batched; single rank only)")
+    ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="12-qubit chunk kernels: 2 = two 6-qubit rounds, 1 = three 4-qubit rounds, "
-                         "0 = rounds chosen per setting")
+                         "0 = rounds chosen per setting, -1 = the plan's automatic choice")
     return ap.parse_args()
 
 
@@ -158,6 +160,60 @@ def cpu_oracle_rate(inst, budget_s, settings_per_call=1, max_settings=None):
         t_total += time.perf_counter() - t0
         done += hi - lo
     return done, t_total
+
+
+def batched_eval(flush, reps=10):
+    """The batched workload (64 independent instances, n uniform in 6..14, rank
+    1..8, K = 2 rank, 200..3000 settings, 500..5000 shots; synth.make_batch(seed=0)):
+    one forward + adjoint of every instance per evaluation, through qst.Batch (one
+    CUDA graph launch) and, for comparison, through one plan per instance called
+    in sequence.  CUDA events on the current stream, L2 flushed before each
+    timed evaluation."""
+    import torch
+    from paper_2607_19577_b300 import qst, synth
+    insts = synth.make_batch(seed=0, count=64)
+    amps = sum(i.M * i.K * (1 << i.n) for i in insts)
+    datas = [qst.Data.from_numpy(i.n, i.basis, i.row_ptr, i.outcome, i.count, i.shots) for i in insts]
+    psis = [torch.from_numpy(i.psi).cuda() for i in insts]
+    ws_ = [torch.from_numpy(i.w).cuda() for i in insts]
+    losses = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in insts]
+    cs = [torch.zeros(i.nnz, dtype=torch.float32, device="cuda") for i in insts]
+    gs = [torch.zeros_like(p) for p in psis]
+    gws = [torch.zeros_like(w) for w in ws_]
+    batch = qst.Batch([(i.n, i.M, i.K, i.nnz) for i in insts])
+    plans = [qst.Plan(i.n, i.M, i.K, i.nnz, eps=i.eps) for i in insts]
+
+    def graph():
+        batch.evaluate(psis, ws_, datas, losses, cs, gs, gws)
+
+    def sequential():
+        for p, ps, w, d, l, c, g, gw in zip(plans, psis, ws_, datas, losses, cs, gs, gws):
+            p.forward(ps, w, d, c_obs=c, loss=l)
+            p.adjoint(ps, w, d, c, grad_psi=g, grad_w=gw)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        total = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / reps
+
+    t_graph, t_seq = timed(graph), timed(sequential)
+    for p in plans:
+        p.close()
+    batch.close()
+    return {"workload": "64 instances, synth.make_batch(seed=0)", "amplitudes_per_eval": int(amps),
+            "ms_per_eval": t_graph, "value": amps / t_graph * 1e3, "unit": "amplitudes/s",
+            "sequential_ms_per_eval": t_seq, "sequential_value": amps / t_seq * 1e3,
+            "how": "qst.Batch: every instance's forward + adjoint in one captured CUDA graph (forked streams); "
+                   "sequential: one plan per instance, called in order"}
 
 
 def run_reference(args):
@@ -351,6 +407,10 @@ def run_ours(args):
                 "how": "qst_iterate replay (one CUDA graph), Table I schedule (T_alpha = 5), step grid 2^-j, "
                        "from the bench state"}
 
+    batched = None
+    if ws == 1 and not args.no_batched:
+        batched = batched_eval(flush)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         done, t = cpu_oracle_rate(inst, args.cpu_seconds)
@@ -371,7 +431,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-                "algorithm1": algo,
+                "algorithm1": algo, "batched": batched,
                 "gpu_launches": launches, "kernels": kern, "wall_ms_per_step": 1e3 * t_wall / args.steps,
                 "workspace_bytes": plan.workspace_bytes()}
         print(json.dumps(line), flush=True)

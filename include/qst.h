@@ -62,10 +62,12 @@ typedef struct qst_params {
     int reg_bits;         /* amplitudes per thread per round = 2^reg_bits: 4 or 5; 0 = auto */
     int fixed_rounds;     /* 12-qubit chunks only.  2 = two rounds of six qubits, 64 amplitudes per
                              thread, two atoms per CTA (one shared-memory exchange per setting in
-                             the forward, two in the adjoint); 1 = three rounds of four qubits on
-                             fixed qubit groups, 16 amplitudes per thread (compile-time
-                             shared-memory offsets, warp-local middle exchange); 0 = rounds chosen
-                             per setting.  Other values: QST_ERR_INVALID_ARG.  Default 2. */
+                             the forward, two in the adjoint; n <= 16 only, n = 17..20 runs 1);
+                             1 = three rounds of four qubits on fixed qubit groups, 16 amplitudes
+                             per thread (compile-time shared-memory offsets, warp-local middle
+                             exchange); 0 = rounds chosen per setting; -1 = automatic: 2 when a
+                             work bin may hold >= 32 settings, else 1.  Other values:
+                             QST_ERR_INVALID_ARG.  Default -1. */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;

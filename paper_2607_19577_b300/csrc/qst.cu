@@ -1325,7 +1325,7 @@ void qst_params_default(qst_params *p) {
     p->max_bin_settings = 0;
     p->validate = 1;
     p->reg_bits = 0;
-    p->fixed_rounds = 2;
+    p->fixed_rounds = -1;
 }
 
 const char *qst_status_string(qst_status s) {
@@ -1376,12 +1376,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
-    if (prm.fixed_rounds < 0 || prm.fixed_rounds > 2) {
+    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 2) {
         delete p;
         return QST_ERR_INVALID_ARG;
     }
-    p->fx2 = c == 12 && prm.fixed_rounds == 2;
-    p->fx = c == 12 && p->A == 4 && prm.fixed_rounds == 1;
     p->B = prm.norm_settings ? prm.norm_settings : M;
     cudaGetDevice(&p->device);
     int sms = 148;
@@ -1394,6 +1392,16 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         p->smax = (int)(s < 4 ? 4 : s);
     }
     if (p->smax > kMaxBin) p->smax = kMaxBin;
+    // 12-qubit chunk kernels.  The two-round kernels build a 64-amplitude-per-
+    // thread source per unit at 8-12 warps per SM; that pays off only when a
+    // unit runs many settings.  Automatic choice (-1): two rounds when bins may
+    // hold >= 32 settings, else three (n = 12 instances with ~8 settings per
+    // bin measured ~20 % faster with three rounds).  The wide path's units hold
+    // one setting each: it always runs the three-round kernels (264 against
+    // 356 ms on the n = 20 workload).
+    const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (p->smax >= 32 ? 2 : 1);
+    p->fx2 = c == 12 && fr == 2 && !wide;
+    p->fx = c == 12 && p->A == 4 && (fr == 1 || (fr == 2 && wide));
     const int64_t D = (int64_t)1 << n;
     if (wide) {
         p->wide = true;

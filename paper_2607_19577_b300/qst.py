@@ -156,14 +156,14 @@ class Plan:
     """Owns a qst_plan (device workspace for one problem shape)."""
 
     def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
-                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=2):
+                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=-1):
         lib = load()
         prm = _Params()
         lib.qst_params_default(ctypes.byref(prm))
         prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
         prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
         # fixed_rounds (12-qubit chunks): 2 = two 6-qubit rounds, 1 = three 4-qubit
-        # rounds, 0 = per-setting rounds (True / False mean 1 / 0)
+        # rounds, 0 = per-setting rounds, -1 = automatic (True / False mean 1 / 0)
         prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(fixed_rounds)
         h = ctypes.c_void_p()
         _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
