@@ -1230,7 +1230,7 @@ qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int
     for (int g0 = 0; g0 < p->M; g0 += p->wide_G) {
         const int G = (p->M - g0) < p->wide_G ? (p->M - g0) : p->wide_G;
         qst_status rc = launch(p, QST_KERNEL_HIGH, st, [&] {
-            k_high_fwd<<<dim3(tiles, G, p->K), 256, 0, st>>>(psi, p->plans, g0, p->K, p->c, p->wide_T);
+            k_high_fwd<<<dim3(tiles, p->K), kWideT, kWideSmem, st>>>(psi, p->plans, g0, G, p->K, p->c, p->wide_T);
         });
         if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] { k_wide_bins<<<1, 256, 0, st>>>(g0, G, p->bins, p->n_bins); });
         if (rc) return rc;
@@ -1272,7 +1272,7 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
     for (int g0 = 0; g0 < p->M; g0 += p->wide_G) {
         const int G = (p->M - g0) < p->wide_G ? (p->M - g0) : p->wide_G;
         qst_status rc = launch(p, QST_KERNEL_HIGH, st, [&] {
-            k_high_fwd<<<dim3(tiles, G, p->K), 256, 0, st>>>(psi, p->plans, g0, p->K, p->c, p->wide_T);
+            k_high_fwd<<<dim3(tiles, p->K), kWideT, kWideSmem, st>>>(psi, p->plans, g0, G, p->K, p->c, p->wide_T);
         });
         if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] { k_wide_bins<<<1, 256, 0, st>>>(g0, G, p->bins, p->n_bins); });
         if (rc) return rc;
@@ -1296,7 +1296,8 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
             launch_adjoint_units(p, a, units, st);
         });
         if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] {
-            k_high_inv_acc<<<dim3(tiles, p->K), 256, 0, st>>>(p->wide_T, p->plans, g0, G, p->K, p->c, p->wide_acc);
+            k_high_inv_acc<<<dim3(tiles, p->K), kWideT, kWideInvSmem, st>>>(p->wide_T, p->plans, g0, G, p->K, p->c,
+                                                                          p->wide_acc);
         });
         if (rc) return rc;
     }
@@ -1466,6 +1467,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         if (p->fx) {
             cudaFuncSetAttribute(k_forward_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(false).total);
             cudaFuncSetAttribute(k_adjoint_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
+        }
+        if (p->wide) {
+            cudaFuncSetAttribute(k_high_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideSmem);
+            cudaFuncSetAttribute(k_high_inv_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideInvSmem);
         }
         if (p->fx2) {
             cudaFuncSetAttribute(k_forward_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(false).total);

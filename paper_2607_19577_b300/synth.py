@@ -159,7 +159,7 @@ def truth_for(name: str, n: int, rng: np.random.Generator):
         wa, aa = dirichlet_weights(8, rng), random_atoms(n, 8, rng)
         wb, ab = dirichlet_weights(8, rng), random_atoms(n, 8, rng)
         return np.concatenate([0.95 * wa, 0.05 * wb]), np.concatenate([aa, ab])
-    rank = {"n12_m2000_k8": 4, "n20_m1024_k8": 4}.get(name, 4)
+    rank = {"n12_m2000_k8": 4, "n20_m1024_k8": 4, "n20_m64_k8": 4}.get(name, 4)
     return dirichlet_weights(rank, rng), random_atoms(n, rank, rng)
 
 
@@ -169,6 +169,8 @@ WORKLOADS = {
     "n12_m2000_k8": (12, 2000, 1000, 8),
     "n16_m4096_k16": (16, 4096, 2000, 16),
     "n20_m1024_k8": (20, 1024, 10000, 8),
+    # per-launch shape of the n = 20 workload with 1/16 of its settings (profiling)
+    "n20_m64_k8": (20, 64, 10000, 8),
 }
 
 
