@@ -995,6 +995,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_wide.cuh"
 #include "qst_fixed.cuh"
 #include "qst_tworound.cuh"
+#include "qst_single.cuh"
 #include "qst_iterate.cuh"
 
 // ----------------------------------------------------------------- host side
@@ -1176,6 +1177,10 @@ void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t 
         return;
     }
     const int grid = units * p->K;
+    if (p->fx && p->wide) {  // single-setting units
+        k_forward_fx1<<<grid, kFxT, kFx1Smem, st>>>(a);
+        return;
+    }
     if (p->fx) {
         k_forward_fx<<<grid, kFxT, fx_smem(false).total, st>>>(a);
         return;
@@ -1191,6 +1196,10 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a, int units, cudaStream_t 
         return;
     }
     const int grid = units * p->K;
+    if (p->fx && p->wide) {  // single-setting units
+        k_adjoint_fx1<<<grid, kFxT, kFx1Smem, st>>>(a);
+        return;
+    }
     if (p->fx) {
         k_adjoint_fx<<<grid, kFxT, fx_smem(true).total, st>>>(a);
         return;
@@ -1469,6 +1478,8 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_adjoint_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
         }
         if (p->wide) {
+            cudaFuncSetAttribute(k_forward_fx1, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
+            cudaFuncSetAttribute(k_adjoint_fx1, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
             cudaFuncSetAttribute(k_high_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideSmem);
             cudaFuncSetAttribute(k_high_inv_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideInvSmem);
         }
