@@ -128,19 +128,24 @@ def _schedule(t, T_alpha, T_ref):
     return 0
 
 
-@pytest.mark.parametrize("name,n,K,T,T_alpha,T_ref", [("n4_all81", None, 4, 14, 3, 7),
-                                                       ("n12_m60_k6", 12, 6, 9, 4, 0)])
-def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref):
+@pytest.mark.parametrize("name,n,K,T,T_alpha,T_ref,rounds", [("n4_all81", None, 4, 14, 3, 7, -1),
+                                                              ("n12_m60_k6", 12, 6, 9, 4, 0, -1),
+                                                              ("n12_m60_k5", 12, 5, 8, 3, 7, 2)])
+def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref, rounds):
     """qst_iterate (every decision on the device, one captured graph) equals the same
     schedule driven from the host with qst_step: bitwise the same atoms and weights
     and the same J after every iteration.  A second run continues (t0 = T) and a
-    replay of the first run's graph on the same buffers reproduces it."""
+    replay of the first run's graph on the same buffers reproduces it.  The last
+    case runs the two-round chunk kernels (odd K: a CTA with one atom), whose
+    forward honours the device skip flag inside conditional graph nodes."""
     inst = synth.make_instance(name, seed=11, K=K)
     psi0 = inst.psi.astype(np.complex128)
     psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
     psi0 = psi0.astype(np.complex64)
     w0 = inst.w.astype(np.float32)
-    plan = qst.Plan(inst.n, inst.M, K, inst.nnz)
+    plan = qst.Plan(inst.n, inst.M, K, inst.nnz, fixed_rounds=rounds)
+    if rounds == 2:
+        assert plan.geometry()["fixed_rounds"] == 2
     d = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
     # host-driven reference
     hp, hw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
