@@ -173,7 +173,8 @@ class Plan:
 
     def close(self):
         if getattr(self, "_h", None):
-            load().qst_plan_destroy(self._h)
+            if getattr(self, "_owned", True):
+                load().qst_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -437,6 +438,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def plan(self, i):
+        """Instance i's plan (owned by the batch: valid while the batch is open)."""
+        h = ctypes.c_void_p()
+        _check(load().qst_batch_plan(self._h, int(i), ctypes.byref(h)), "qst_batch_plan")
+        p = Plan.__new__(Plan)
+        p._h, p._owned = h, False
+        p.n, p.M, p.K, p.nnz = self.shapes[i]
+        p.D = 1 << p.n
+        return p
 
     def evaluate(self, psis, ws, datas, losses, c_obss, grads, grad_ws):
         """All arguments are lists (one entry per instance) of CUDA tensors."""
