@@ -300,9 +300,9 @@ qst_status qst_iterate(qst_plan plan, int T, int t0, float *psi, float *w,
                        double *J_hist, int *accepted_hist, void *stream);
 
 /*
- * Batched evaluation of many independent instances of uneven shape (the
- * batched workload of the benchmark spec: instances with different n, M, K and
- * shots).  qst_batch_create makes one plan per instance (params shared).
+ * Batched evaluation of many independent instances of uneven shape
+ * (instances with different n, M, K and shots, e.g. 64 instances with n from
+ * 6 to 14).  qst_batch_create makes one plan per instance (params shared).
  * qst_batch_evaluate runs every instance's qst_forward + qst_adjoint; arguments
  * are HOST arrays of `count` DEVICE pointers, one per instance, with the
  * per-instance layouts of qst_forward / qst_adjoint (loss[i] -> double[1],
