@@ -262,6 +262,17 @@ def test_parity_fixed_and_per_setting_rounds(n, fixed):
     compare(inst, run_gpu(inst, dense=dense, fixed_rounds=fixed), run_oracle(inst, dense=dense), dense=dense)
 
 
+@pytest.mark.parametrize("n,M,K,smax,seed", [(12, 23, 1, 96, 0), (12, 31, 2, 3, 1), (13, 29, 5, 1, 2),
+                                              (14, 40, 1, 7, 3), (15, 18, 3, 96, 4), (16, 9, 1, 2, 5)])
+def test_parity_two_round_bins_and_atoms(n, M, K, smax, seed):
+    """The two-round kernels with one atom per CTA (K = 1, odd K), bins split to
+    a few settings or a single one, and 0..4 high bits, against the oracle."""
+    inst = synth.random_instance(n, M, K, 600, 900 + seed)
+    dense = n <= 12
+    compare(inst, run_gpu(inst, dense=dense, fixed_rounds=2, max_bin_settings=smax), run_oracle(inst, dense=dense),
+            dense=dense)
+
+
 @pytest.mark.parametrize("n,M,K,seed", [(5, 14, 3, 0), (12, 20, 4, 1), (16, 6, 2, 2)])
 def test_tangent_matches_oracle(n, M, K, seed):
     """qst_tangent (Eq. atom-projected-descent-direction) from the adjoint's outputs,
