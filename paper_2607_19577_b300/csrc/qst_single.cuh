@@ -51,13 +51,13 @@ __global__ void __launch_bounds__(kFxT, 4) k_forward_fx1(const FwdArgs a) {
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
     constexpr uint32_t cmask = 4095u;
-    const Fx1Unit us = fx1_unit(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff);
-    float2 v[16];
+    float2 v[16];  // the source loads go out before the setting's metadata chain
     {
         const float2 *psik = a.psi + (size_t)bin * a.src_bin_stride + (size_t)k * D;
         build_source_regs<12, 4, 0, 8>(v, psik, f, b.xytop, b.ytop, tid);
         build_source_regs<12, 4, 8, 8>(v, psik, f, b.xytop, b.ytop, tid);
     }
+    const Fx1Unit us = fx1_unit(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff);
     const uint32_t b0 = fx_pidx(fx_ubase<0>(tid)), b1 = fx_pidx(fx_ubase<1>(tid)), b2 = fx_pidx(fx_ubase<2>(tid));
 #pragma unroll
     for (int R = 0; R < 3; ++R) {
@@ -98,14 +98,14 @@ __global__ void __launch_bounds__(kFxT, 4) k_adjoint_fx1(const AdjArgs a) {
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
     constexpr uint32_t cmask = 4095u;
-    const Fx1Unit us = fx1_unit(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff);
-    for (int u = tid; u < kFxBuf; u += kFxT) cden[u] = 0.f;
-    float2 v[16];
+    float2 v[16];  // the source loads go out before the setting's metadata chain
     {
         const float2 *psik = a.psi + (size_t)bin * a.src_bin_stride + (size_t)k * D;
         build_source_regs<12, 4, 0, 8>(v, psik, f, b.xytop, b.ytop, tid);
         build_source_regs<12, 4, 8, 8>(v, psik, f, b.xytop, b.ytop, tid);
     }
+    const Fx1Unit us = fx1_unit(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff);
+    for (int u = tid; u < kFxBuf; u += kFxT) cden[u] = 0.f;
     __syncthreads();  // the buffer is zeroed before any entry is scattered
     for (int j = tid; j < us.cnt; j += kFxT)
         cden[fx_pidx(a.outcome[us.lo + j] & cmask)] = a.c_obs[us.lo + j] * us.cs;
