@@ -17,7 +17,12 @@ Parity pins (tests/test_oracle_*.py): dense brute force with explicit Kronecker
 matrices, closed forms (|0...0>, GHZ, product states), linear inversion on the
 full n=4 Pauli set, POVM completeness (c == 1 gives G v = v), the identities
 <psi_k|G psi_k> = h_k and sum_k w_k h_k = sum pihat*pi/(pi+eps), and central
-finite differences of the loss.  No function here is unpinned.
+finite differences of the loss.  The update-rule helpers are pinned too:
+simplex projection by its KKT conditions, refactor by dense eigh of rho, the
+Krylov Ritz pairs by dense eigenpairs of S, and every slot of ``step`` (accepted
+flag, step size, J and state) plus ``tangent`` (dense projector, and the rate
+-2||d||^2 of the objective along the normalised trial) against a route built
+from dense D x D matrices.  No function here is unpinned.
 """
 from __future__ import annotations
 

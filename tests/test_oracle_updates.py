@@ -229,3 +229,198 @@ def test_oracle_spectral_slot_is_monotone_and_feasible():
         if J_prev is not None:
             assert J <= J_prev + 1e-15
         J_prev = J
+
+
+# ----------------------------------------------------------------- Algorithm 1 slots against a dense route
+#
+# The helpers below recompute every slot of Algorithm 1 from dense matrices: rho as a
+# D x D matrix, p_s from the diagonal of V_s rho V_s^* with Kronecker V_s, G as
+# sum_m c_m E_m, the tangent with the explicit projector I - psi psi^*, the simplex
+# projection by bisection on its threshold, and the spectral candidates from a dense
+# eigh of S = rho + eta G.  None of them calls the oracle.
+
+STEP_EPS, STEP_MU, STEP_TAU, STEP_TAU_ACC = 1e-8, 1e-3, 1e-3, 1e-10
+GRID = [2.0 ** -j for j in range(11)]  # Table I step grid, largest first
+
+
+def _dense_objective(inst, psi, w):
+    """J = -sum pihat log(p/B + eps) + mu #{w > 0} from dense probabilities; also c."""
+    from test_oracle_pins import dense_rotation
+    psi = np.asarray(psi, complex)
+    rho = (psi.T * np.asarray(w)) @ psi.conj()
+    M = inst.basis.shape[0]
+    L, c = 0.0, np.zeros(inst.outcome.shape[0])
+    for s in range(M):
+        U = dense_rotation(inst.basis[s])
+        p = np.real(np.einsum("ud,de,ue->u", U, rho, U.conj()))
+        for i in range(inst.row_ptr[s], inst.row_ptr[s + 1]):
+            pihat = inst.count[i] / (M * inst.shots[s])
+            pi = p[inst.outcome[i]] / M
+            L -= pihat * np.log(pi + STEP_EPS)
+            c[i] = pihat / (pi + STEP_EPS)
+    return L + STEP_MU * int(np.count_nonzero(np.asarray(w) > 0)), c
+
+
+def _dense_G(inst, c):
+    from test_oracle_pins import dense_rotation
+    D, M = 1 << inst.n, inst.basis.shape[0]
+    G = np.zeros((D, D), complex)
+    for s in range(M):
+        U = dense_rotation(inst.basis[s])
+        for i in range(inst.row_ptr[s], inst.row_ptr[s + 1]):
+            row = U[int(inst.outcome[i])]
+            G += c[i] * np.outer(row.conj(), row) / M
+    return G
+
+
+def _proj_bisect(v):
+    """Euclidean projection onto the simplex as max(v - theta, 0) with theta found by
+    bisection on sum max(v - theta, 0) = 1 (a different route from sorting)."""
+    v = np.asarray(v, float)
+    lo, hi = v.min() - 1.0, v.max()
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.maximum(v - mid, 0.0).sum() > 1.0:
+            lo = mid
+        else:
+            hi = mid
+    b = np.maximum(v - 0.5 * (lo + hi), 0.0)
+    return b / b.sum()
+
+
+def _prune_dense(beta):
+    keep = [i for i in range(len(beta)) if beta[i] > STEP_TAU]
+    if not keep:
+        keep = [int(np.argmax(beta))]
+    b = np.asarray([beta[i] for i in keep])
+    return keep, b / b.sum()
+
+
+def _dense_step(inst, psi, w, slot, r):
+    """(psi~, w~, J, accepted, eta) of one Algorithm 1 slot, dense route."""
+    psi = np.array(psi, complex)
+    w = np.array(w, float)
+    K, D = psi.shape
+    J0, c0 = _dense_objective(inst, psi, w)
+    G = _dense_G(inst, c0)
+    rho = (psi.T * w) @ psi.conj()
+    if slot == 2:
+        act = int(np.count_nonzero(w > 0))
+        lam, V = np.linalg.eigh(rho)
+        lam, V = lam[::-1][:act], V[:, ::-1][:, :act]
+        lam = np.maximum(lam, 0.0)
+        keep, b = _prune_dense(lam / lam.sum())
+        pt, wt = np.zeros_like(psi), np.zeros_like(w)
+        pt[:len(keep)] = V[:, keep].T
+        wt[:len(keep)] = b
+        Jt, _ = _dense_objective(inst, pt, wt)
+        return (pt, wt, Jt, True, 0.0) if Jt <= J0 - STEP_TAU_ACC else (psi, w, J0, False, 0.0)
+    for eta in GRID:
+        if slot == 0:
+            x = psi[r]
+            P = np.eye(D) - np.outer(x, x.conj())
+            d = w[r] * (P @ (G @ x))
+            t = x + eta * d
+            pt, wt = psi.copy(), w
+            pt[r] = t / np.linalg.norm(t)
+        elif slot == 1:
+            h = np.real(np.einsum("kd,de,ke->k", psi.conj(), G, psi))
+            act = np.nonzero(w > 0)[0]
+            keep, b = _prune_dense(_proj_bisect(w[act] + eta * h[act]))
+            pt, wt = psi, np.zeros_like(w)
+            wt[act[keep]] = b
+        else:  # slot 3: exact eigenpairs of S = rho + eta G (the Krylov space is all of C^D here)
+            lam, V = np.linalg.eigh(rho + eta * G)
+            lam, V = lam[::-1], V[:, ::-1]
+            best = None
+            for s_ in range(1, min(K, D) + 1):
+                keep, b = _prune_dense(_proj_bisect(lam[:s_]))
+                q = (np.dot(b, b) - 2.0 * np.dot(b, lam[keep])) / (2.0 * eta) + STEP_MU * len(keep)
+                if best is None or q < best[0]:
+                    best = (q, keep, b)
+            _, keep, b = best
+            pt, wt = np.zeros_like(psi), np.zeros_like(w)
+            pt[:len(keep)] = V[:, keep].T
+            wt[:len(keep)] = b
+        Jt, _ = _dense_objective(inst, pt, wt)
+        if Jt <= J0 - STEP_TAU_ACC:
+            return pt, wt, Jt, True, eta
+    return psi, w, J0, False, GRID[-1]
+
+
+def _rho_of(psi, w):
+    return (np.asarray(psi).T * np.asarray(w)) @ np.asarray(psi).conj()
+
+
+def _step_case(seed, K, shots):
+    inst = synth.make_instance("n4_all81", seed=seed, K=K, shots=shots)
+    psi = inst.psi.astype(np.complex128)
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    w = synth.dirichlet_weights(K, synth.rng_for(seed, 55))  # distinct, non-uniform weights
+    return inst, psi, w
+
+
+@pytest.mark.parametrize("seed,K,shots", [(3, 4, 1000), (8, 3, 200)])
+def test_oracle_step_equals_dense_route(seed, K, shots):
+    """Every slot of oracle.step against the dense route: the same accepted flag, the
+    same eta from the Table I grid, the same J, and the same state (compared through
+    rho, which is free of atom phases and of the basis of degenerate eigenspaces).
+    The sequence must accept in the three step-grid slot kinds and at least once below
+    eta = 1; the refactor (slot 2) is accepted only when it lowers the rank, which the
+    second half checks on a state with a duplicated atom."""
+    inst, psi, w = _step_case(seed, K, shots)
+    data = _data(inst)
+    accepted, etas = set(), []
+    for slot, r in [(0, 0), (0, 1), (1, 0), (3, 0), (0, 2), (1, 0), (2, 0), (0, 0), (3, 0), (1, 0)]:
+        if slot == 0 and r >= K:
+            continue
+        po, wo, Jo, acc_o, eta_o = oracle.step(4, data, psi, w, slot, r)
+        pd, wd, Jd, acc_d, eta_d = _dense_step(inst, psi, w, slot, r)
+        assert acc_o == acc_d and eta_o == eta_d, (slot, r, acc_o, acc_d, eta_o, eta_d)
+        assert abs(Jo - Jd) <= 1e-10 * max(1.0, abs(Jd)), (slot, Jo, Jd)
+        np.testing.assert_allclose(_rho_of(po, wo), _rho_of(pd, wd), atol=1e-10)
+        if acc_o:
+            accepted.add(slot)
+            etas.append(eta_o)
+        psi, w = po, wo
+    assert {0, 1, 3} <= accepted, accepted
+    assert any(0.0 < e < 1.0 for e in etas), etas
+    # a duplicated atom: the refactor merges the two copies (rank K - 1), so mu R drops
+    psi[1] = psi[0]
+    w = np.full(K, 1.0 / K)
+    po, wo, Jo, acc_o, _ = oracle.step(4, data, psi, w, 2, 0)
+    pd, wd, Jd, acc_d, _ = _dense_step(inst, psi, w, 2, 0)
+    assert acc_o and acc_d and np.count_nonzero(wo > 0) == K - 1
+    assert abs(Jo - Jd) <= 1e-10 * max(1.0, abs(Jd))
+    np.testing.assert_allclose(_rho_of(po, wo), _rho_of(pd, wd), atol=1e-10)
+
+
+@pytest.mark.parametrize("n,K,seed", [(3, 3, 4), (4, 4, 6)])
+def test_oracle_tangent_against_dense_projector_and_fd(n, K, seed):
+    """oracle.tangent = w_k (I - psi_k psi_k^*) G psi_k with the projector as a dense
+    matrix and distinct, non-unit weights; along the normalised trial
+    (psi_k + t d_k)/||psi_k + t d_k|| the objective changes at rate -2 ||d_k||^2
+    (central differences of the dense objective), which fixes the w_k factor."""
+    inst = synth.random_instance(n, 3 ** n if n <= 3 else 40, K, shots=400, seed=seed)
+    psi = inst.psi.astype(np.complex128)
+    psi /= np.linalg.norm(psi, axis=1, keepdims=True)
+    w = np.array([0.55, 0.3, 0.1, 0.05][:K])
+    w = w / w.sum()
+    J0, c = _dense_objective(inst, psi, w)
+    G = _dense_G(inst, c)
+    Gpsi = (G @ psi.T).T
+    d = oracle.tangent(psi, w, Gpsi)
+    D = 1 << n
+    for k in range(K):
+        P = np.eye(D) - np.outer(psi[k], psi[k].conj())
+        np.testing.assert_allclose(d[k], w[k] * (P @ Gpsi[k]), atol=1e-14)
+        t = 1e-5
+        vals = []
+        for sgn in (1, -1):
+            x = psi[k] + sgn * t * d[k]
+            pt = psi.copy()
+            pt[k] = x / np.linalg.norm(x)
+            vals.append(_dense_objective(inst, pt, w)[0])
+        fd = (vals[0] - vals[1]) / (2 * t)
+        want = -2.0 * np.sum(np.abs(d[k]) ** 2)
+        assert abs(fd - want) <= 1e-6 * abs(want) + 1e-12, (k, fd, want)
