@@ -345,6 +345,14 @@ qst_status qst_batch_evaluate(qst_batch batch, const float *const *psi, const fl
  * (bins) x K x 2^n x 8 bytes plus a few bytes per setting.  For example,
  * n = 12, M = 2000, K = 8 fits, while n = 16, K = 16 does not.
  *
+ * Limits beyond the scratch size: n <= 16 with at most 4 qubits above the
+ * chunk (n = 17..20, or a chunk_qubits that leaves more, returns
+ * QST_ERR_UNSUPPORTED), and the call always runs the per-setting-round chunk
+ * kernels that a plan with fixed_rounds = 0 runs, never the two-round or
+ * fixed-round kernels a plan may choose.  So params->fixed_rounds must be -1
+ * or 0 (anything else returns QST_ERR_INVALID_ARG), and results agree with a
+ * plan's within rounding, not bit for bit.
+ *
  * The first call on each device looks up the array's device address and sets
  * kernel attributes, so make that first call before any stream capture.
  * Every call shares the one array, and it keeps the last call's contents.

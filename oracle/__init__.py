@@ -151,6 +151,73 @@ def apply_G(n, basis, row_ptr, outcome, c_obs, v, B=None):
     return out
 
 
+def _shards(M, parts):
+    """Contiguous setting ranges [lo, hi) covering 0..M-1, at most `parts` of them."""
+    parts = max(1, min(int(parts), M)) if M else 1
+    edges = [round(M * j / parts) for j in range(parts + 1)]
+    return [(edges[j], edges[j + 1]) for j in range(parts) if edges[j + 1] > edges[j]] or [(0, 0)]
+
+
+def _threads(threads):
+    if threads:
+        return int(threads)
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def forward_sharded(n, basis, psi, w, row_ptr, outcome, count, shots, eps=1e-8, B=None, threads=None):
+    """forward() over contiguous setting shards on a thread pool (the measurement
+    partition of Sec. III-B: every shard uses the global B, so the per-entry
+    outputs are those of forward() and the loss is the sum of the shard losses,
+    added in shard order).  The C routine releases the GIL, so the shards run on
+    separate host cores.  The arithmetic per setting is forward()'s."""
+    from concurrent.futures import ThreadPoolExecutor
+    basis = _c(basis, np.uint8)
+    M = basis.shape[0]
+    row_ptr = _c(row_ptr, np.int64)
+    B = int(B or M)
+    parts = _shards(M, _threads(threads))
+
+    def run(r):
+        lo, hi = r
+        a, b = int(row_ptr[lo]), int(row_ptr[hi])
+        return forward(n, basis[lo:hi], psi, w, row_ptr[lo:hi + 1] - a, outcome[a:b], count[a:b], shots[lo:hi],
+                       eps=eps, B=B)
+    with ThreadPoolExecutor(len(parts)) as ex:
+        res = list(ex.map(run, parts))
+    loss = 0.0
+    for r in res:
+        loss += r["loss"]
+    return dict(p_obs=np.concatenate([r["p_obs"] for r in res]), c_obs=np.concatenate([r["c_obs"] for r in res]),
+                loss=loss)
+
+
+def adjoint_sharded(n, basis, psi, w, row_ptr, outcome, c_obs, B=None, threads=None):
+    """adjoint() over contiguous setting shards on a thread pool, summed in shard
+    order (G psi, h and the gradients are sums over settings, Eqs.
+    negative-gradient-product and weight-gradient; each shard uses the global B).
+    The arithmetic per setting is adjoint()'s."""
+    from concurrent.futures import ThreadPoolExecutor
+    basis = _c(basis, np.uint8)
+    M = basis.shape[0]
+    row_ptr = _c(row_ptr, np.int64)
+    c_obs = _c(c_obs, np.float64)
+    B = int(B or M)
+    parts = _shards(M, _threads(threads))
+
+    def run(r):
+        lo, hi = r
+        a, b = int(row_ptr[lo]), int(row_ptr[hi])
+        return adjoint(n, basis[lo:hi], psi, w, row_ptr[lo:hi + 1] - a, outcome[a:b], c_obs[a:b], B=B)
+    with ThreadPoolExecutor(len(parts)) as ex:
+        res = list(ex.map(run, parts))
+    out = {key: res[0][key].copy() for key in ("G_psi", "grad_psi", "h")}
+    for r in res[1:]:
+        for key in out:
+            out[key] += r[key]
+    out["grad_w"] = -out["h"]
+    return out
+
+
 def amplitude(n, b, psi, u):
     """(V_s psi)_u by direct summation over all basis states (independent of the
     axis-by-axis transform)."""

@@ -2372,6 +2372,8 @@ extern "C" qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz, cons
     qst_params_default(&prm);
     if (params) prm = *params;
     if (!(prm.eps >= 0.0) || prm.norm_settings < 0 || prm.max_bin_settings < 0) return QST_ERR_INVALID_ARG;
+    // always the per-setting-round kernels: a request for another family is refused
+    if (prm.fixed_rounds != -1 && prm.fixed_rounds != 0) return QST_ERR_INVALID_ARG;
     const int c = prm.chunk_qubits ? prm.chunk_qubits : (n < kMaxChunk ? n : kMaxChunk);
     if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
     const int r = n - c;

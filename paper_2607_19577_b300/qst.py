@@ -388,15 +388,50 @@ QST_ERR_SCRATCH_TOO_SMALL = 6
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
+def _noalloc_args(psi, w, d: Data, c_obs, grad_psi, grad_w, device_status):
+    """Every check qst_adjoint_noalloc's arguments need before their pointers reach
+    the library: dtypes, shapes and contiguity first (Plan.adjoint's and Data's
+    checks), then that every tensor is on the current CUDA device (the library
+    takes its scratch and launches on that device).  Returns n."""
+    if not isinstance(psi, torch.Tensor) or psi.dim() != 2:
+        raise QSTError("psi must be a 2-D complex64 tensor [K][2^n]")
+    K, D = psi.shape
+    if K < 1 or D < 2 or D & (D - 1):
+        raise QSTError(f"psi: expected [K >= 1][2^n], a power of two with n >= 1, got {tuple(psi.shape)}")
+    n = D.bit_length() - 1
+    if d.n != n:
+        raise QSTError(f"data is for n = {d.n} qubits, psi for n = {n}")
+    M, nnz = d.basis.shape[0], d.outcome.shape[0]
+    named = [(psi, torch.complex64, (K, D), "psi"), (w, torch.float32, (K,), "w"),
+             (grad_psi, torch.complex64, (K, D), "grad_psi"), (grad_w, torch.float32, (K,), "grad_w"),
+             (c_obs, torch.float32, (nnz,), "c_obs"), (device_status, torch.int32, (1,), "device_status"),
+             (d.basis, torch.uint8, (M, n), "basis"), (d.row_ptr, torch.int64, (M + 1,), "row_ptr"),
+             (d.outcome, torch.int32, (nnz,), "outcome"), (d.count, torch.int32, (nnz,), "count"),
+             (d.shots, torch.int32, (M,), "shots")]
+    for t, dt, shape, name in named:
+        if not isinstance(t, torch.Tensor):
+            raise QSTError(f"{name} must be a tensor")
+        if t.dtype != dt or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise QSTError(f"{name}: expected contiguous {dt} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    for t, _, _, name in named:
+        if not t.is_cuda:
+            raise QSTError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise QSTError(f"{name} is on cuda:{t.device.index}, the current device is "
+                           f"cuda:{torch.cuda.current_device()}")
+    return n
+
+
 def adjoint_noalloc(psi, w, d: Data, c_obs, grad_psi, grad_w, device_status, params=None):
     """qst_adjoint_noalloc: the adjoint for callers that cannot allocate device
     memory (their workspace would otherwise come from cudaMalloc).  Every
-    argument is a caller-owned CUDA tensor; device_status is an int32 [1]
-    tensor that receives the device-side data-check bits.  Returns the status
-    code (QST_ERR_SCRATCH_TOO_SMALL when the problem needs more than the
-    library's fixed scratch)."""
-    K, D = psi.shape
-    n = D.bit_length() - 1
+    argument is a caller-owned CUDA tensor on the current device; device_status
+    is an int32 [1] tensor that receives the device-side data-check bits.
+    Arguments are checked here (QSTError) before any pointer reaches the
+    library.  Returns the status code (QST_ERR_SCRATCH_TOO_SMALL when the
+    problem needs more than the library's fixed scratch)."""
+    n = _noalloc_args(psi, w, d, c_obs, grad_psi, grad_w, device_status)
+    K = psi.shape[0]
     prm = None
     if params is not None:
         prm = _Params()

@@ -86,3 +86,32 @@ def test_full_batched_workload_equals_single_plans():
         inner = np.sum(np.conj(psi) * (-g.cpu().numpy().astype(np.complex128) / w[:, None]), axis=1).real
         np.testing.assert_allclose(inner, -gw.cpu().numpy(), rtol=1e-4)
     b.close()
+
+
+def test_full_batched_workload_largest_instances_match_oracle():
+    """The instances of the full 64-instance workload with the most qubits (n = 14,
+    and the largest n = 13 one), evaluated in the batch, against the FP64 oracle
+    over all of their settings (sharded over the host cores)."""
+    insts = synth.make_batch(seed=0, count=64)
+    b = qst.Batch([(i.n, i.M, i.K, i.nnz) for i in insts])
+    datas, psis, ws, losses, cs, gs, gws = _alloc(insts)
+    b.evaluate(psis, ws, datas, losses, cs, gs, gws)
+    torch.cuda.synchronize()
+    pick = []
+    for n in (14, 13):
+        cand = [j for j, i in enumerate(insts) if i.n == n]
+        pick += sorted(cand, key=lambda j: -insts[j].M * insts[j].K)[:1 if n == 13 else 2]
+    assert pick
+    for j in pick:
+        inst = insts[j]
+        psi, w = inst.psi.astype(np.complex128), inst.w.astype(np.float64)
+        f = oracle.forward_sharded(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+        c = cs[j].cpu().numpy().astype(np.float64)
+        a = oracle.adjoint_sharded(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, c)
+        assert abs(losses[j].item() - f["loss"]) <= 1e-5 * abs(f["loss"])
+        np.testing.assert_allclose(c, f["c_obs"], rtol=1e-4)
+        gg = gs[j].cpu().numpy().astype(np.complex128)
+        for k in range(inst.K):
+            assert np.max(np.abs(gg[k] - a["grad_psi"][k])) <= 1e-4 * np.max(np.abs(a["grad_psi"][k])), (j, k)
+        np.testing.assert_allclose(gws[j].cpu().numpy(), a["grad_w"], rtol=1e-4)
+    b.close()

@@ -119,3 +119,57 @@ def test_povm_completeness_at_n16():
     err = (g - psi).abs().max().item() / psi.abs().max().item()
     assert err <= 1e-5
     plan.close()
+
+
+@pytest.fixture(scope="module")
+def c3k2():
+    """The bench workload's settings and counts with its first two atoms (w = 1/2 each)
+    in the bench's per-unit launch configuration: two-round chunk kernels and bins of
+    up to 96 settings (a plan for K = 16 chooses both on its own)."""
+    inst = synth.make_instance("n16_m4096_k16", seed=0)
+    inst.psi = np.ascontiguousarray(inst.psi[:2])
+    inst.w = np.full(2, 0.5, np.float32)
+    plan = qst.Plan(inst.n, inst.M, 2, inst.nnz, fixed_rounds=2, max_bin_settings=96)
+    assert plan.geometry()["fixed_rounds"] == 2
+    data = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    psi, w = torch.from_numpy(inst.psi).cuda(), torch.from_numpy(inst.w).cuda()
+    p_obs, c_obs, loss = plan.forward(psi, w, data)
+    g, gw = plan.adjoint(psi, w, data, c_obs)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    out = dict(inst=inst, p_obs=p_obs.cpu().numpy().astype(np.float64), c_obs=c_obs.cpu().numpy().astype(np.float64),
+               loss=loss.item(), g=g.cpu().numpy().astype(np.complex128), gw=gw.cpu().numpy().astype(np.float64))
+    plan.close()
+    return out
+
+
+def test_all_settings_forward_k2(c3k2):
+    """p and c at every observed outcome of all 4096 settings against the FP64 oracle
+    (settings sharded over the host cores).  The p error is taken relative to the
+    largest observed p of its setting, which is no larger than the setting's largest
+    p, so the bound is at least as strict as the normwise one."""
+    inst = c3k2["inst"]
+    ref = oracle.forward_sharded(inst.n, inst.basis, inst.psi.astype(np.complex128), inst.w.astype(np.float64),
+                                 inst.row_ptr, inst.outcome, inst.count, inst.shots, eps=inst.eps)
+    p = c3k2["p_obs"]
+    worst = 0.0
+    for s in range(inst.M):
+        lo, hi = inst.row_ptr[s], inst.row_ptr[s + 1]
+        r = ref["p_obs"][lo:hi]
+        worst = max(worst, np.max(np.abs(p[lo:hi] - r)) / np.max(r))
+    assert worst <= P_TOL, worst
+    np.testing.assert_allclose(c3k2["c_obs"], ref["c_obs"], rtol=C_TOL)
+    assert abs(c3k2["loss"] - ref["loss"]) <= 1e-5 * abs(ref["loss"])
+
+
+def test_all_settings_adjoint_k2(c3k2):
+    """G psi_k summed over all 4096 settings, element by element against the FP64
+    oracle given the same c (the sum over settings of the headline size)."""
+    inst = c3k2["inst"]
+    ref = oracle.adjoint_sharded(inst.n, inst.basis, inst.psi.astype(np.complex128), inst.w.astype(np.float64),
+                                 inst.row_ptr, inst.outcome, c3k2["c_obs"])
+    for k in range(2):
+        nrm = np.max(np.abs(ref["grad_psi"][k]))
+        err = np.max(np.abs(c3k2["g"][k] - ref["grad_psi"][k])) / nrm
+        assert err <= G_TOL, (k, err)
+    np.testing.assert_allclose(c3k2["gw"], ref["grad_w"], rtol=H_TOL)

@@ -3,7 +3,10 @@
 Tolerances (FP32 path against FP64; the rotation is add-only, so each of the
 <= n butterfly stages adds at most one rounding of relative size 2^-24 to every
 amplitude, and |.|^2 doubles it):
-  * probabilities: per setting max_u |dp_u| / max_u p_u <= 1e-5
+  * probabilities: per setting max_u |dp_u| / max_u p_u <= 1e-5, the maximum of
+    p taken over all 2^n outcomes of the setting (the normwise error of the
+    setting's distribution), the difference over the outcomes the kernel
+    outputs (all of them for the dense output, the observed ones for p_obs)
   * likelihood ratio c: relative 1e-4; loss: relative 1e-5
   * gradients: per atom ||d grad_k||_inf / ||grad_k||_inf <= 1e-4; h: relative 1e-4
 """
@@ -38,13 +41,27 @@ def run_gpu(inst, dense=False, **plan_kw):
     return out
 
 
+def setting_pmax(n, basis, psi, w):
+    """max_u p_{s,u} over all 2^n outcomes of every setting (FP64 oracle, dense)."""
+    M, D = basis.shape[0], 1 << n
+    step = max(1, (1 << 24) // D)
+    out = np.zeros(M)
+    for lo in range(0, M, step):
+        hi = min(M, lo + step)
+        f = oracle.forward(n, basis[lo:hi], psi, w, np.zeros(hi - lo + 1, np.int64), np.zeros(0, np.uint32),
+                           np.zeros(0, np.uint32), np.ones(hi - lo, np.uint32), dense=True)
+        out[lo:hi] = f["p_dense"].max(axis=1)
+    return out
+
+
 def run_oracle(inst, dense=False):
     psi = inst.psi.astype(np.complex128)
     w = inst.w.astype(np.float64)
     f = oracle.forward(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots,
                        eps=inst.eps, dense=dense)
     a = oracle.adjoint(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, f["c_obs"])
-    return {**f, **a}
+    pmax = f["p_dense"].max(axis=1) if dense else setting_pmax(inst.n, inst.basis, psi, w)
+    return {**f, **a, "p_max": pmax}
 
 
 def compare(inst, gpu, ref, dense=False):
@@ -54,8 +71,9 @@ def compare(inst, gpu, ref, dense=False):
     for s in range(inst.M):
         lo, hi = inst.row_ptr[s], inst.row_ptr[s + 1]
         if hi > lo:
-            scale = max(np.max(ref["p_obs"][lo:hi]), 1e-300)
-            assert np.max(np.abs(gpu["p_obs"][lo:hi] - ref["p_obs"][lo:hi])) / scale <= P_TOL * 4
+            scale = max(ref["p_max"][s], 1e-300)
+            err = np.max(np.abs(gpu["p_obs"][lo:hi] - ref["p_obs"][lo:hi])) / scale
+            assert err <= P_TOL, (s, err)
     if inst.nnz:
         np.testing.assert_allclose(gpu["c_obs"], ref["c_obs"], rtol=C_TOL, atol=1e-12)
     assert abs(gpu["loss"] - ref["loss"]) <= L_TOL * max(abs(ref["loss"]), 1e-30)

@@ -346,3 +346,24 @@ def test_sharded_sums_equal_unsharded():
     assert abs(L - full["loss"]) < 1e-13 * max(1, abs(L))
     np.testing.assert_allclose(h, fadj["h"], rtol=1e-13)
     np.testing.assert_allclose(G, fadj["G_psi"], atol=1e-15)
+
+
+def test_sharded_oracle_equals_the_serial_oracle():
+    """forward_sharded / adjoint_sharded (contiguous setting shards on host threads,
+    summed in shard order) give the serial oracle's values: per-entry outputs
+    exactly, sums to rounding."""
+    inst = synth.random_instance(7, 23, 3, 300, 41)
+    psi = inst.psi.astype(np.complex128)
+    w = inst.w.astype(np.float64)
+    f1 = oracle.forward(7, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    a1 = oracle.adjoint(7, inst.basis, psi, w, inst.row_ptr, inst.outcome, f1["c_obs"])
+    for threads in (1, 3, 8):
+        f2 = oracle.forward_sharded(7, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots,
+                                    threads=threads)
+        np.testing.assert_array_equal(f2["p_obs"], f1["p_obs"])
+        np.testing.assert_array_equal(f2["c_obs"], f1["c_obs"])
+        assert abs(f2["loss"] - f1["loss"]) <= 1e-14 * abs(f1["loss"])
+        a2 = oracle.adjoint_sharded(7, inst.basis, psi, w, inst.row_ptr, inst.outcome, f1["c_obs"], threads=threads)
+        np.testing.assert_allclose(a2["G_psi"], a1["G_psi"], rtol=0, atol=1e-14 * np.max(np.abs(a1["G_psi"])))
+        np.testing.assert_allclose(a2["h"], a1["h"], rtol=1e-13)
+        np.testing.assert_allclose(a2["grad_w"], a1["grad_w"], rtol=1e-13)
