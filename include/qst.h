@@ -68,6 +68,12 @@ typedef struct qst_params {
                              exchange); 0 = rounds chosen per setting; -1 = automatic: 2 when a
                              work bin may hold >= 32 settings, else 1.  Other values:
                              QST_ERR_INVALID_ARG.  Default -1. */
+    int phi_cache;        /* qst_evaluate's transform cache (two-round plans only): the forward stores
+                             the chunk transform of every atom at every observed outcome (K x nnz
+                             complex64, owned by the plan) and the adjoint then runs its inverse
+                             rounds only.  1 = on (QST_ERR_UNSUPPORTED for other plans), 0 = off,
+                             -1 = automatic: on for two-round plans when K x nnz x 8 bytes <= 16 GiB.
+                             qst_forward and qst_adjoint never use it.  Default -1. */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;
@@ -136,8 +142,27 @@ qst_status qst_adjoint(qst_plan plan, const float *psi, const float *w,
                        float *grad_psi, float *grad_w, void *stream);
 
 /*
+ * Forward and adjoint of one evaluation in one call (Eqs. atomic-born-map,
+ * qst-loss, likelihood-ratio-vector, then negative-gradient-product,
+ * atom-wirtinger-gradient, weight-gradient): the outputs of qst_forward
+ * (p_obs and loss may be NULL; c_obs is required and receives c) followed by
+ * those of qst_adjoint with that c, all device pointers, asynchronous on
+ * `stream`.  With the plan's transform cache (qst_params.phi_cache) the
+ * forward stores the rotated amplitudes at the observed outcomes and the
+ * adjoint applies only the inverse rotations to c .* (V_s psi_k) instead of
+ * recomputing V_s psi_k (the paper's optional response storage, Sec. III-B,
+ * kept for the observed outcomes only); the results agree with separate
+ * qst_forward / qst_adjoint calls within rounding.  Without the cache it is
+ * exactly those two calls.  Same errors as qst_forward and qst_adjoint.
+ */
+qst_status qst_evaluate(qst_plan plan, const float *psi, const float *w, const uint8_t *basis,
+                        const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
+                        const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
+                        float *grad_psi, float *grad_w, void *stream);
+
+/*
  * Forward then adjoint from HOST buffers: copies the inputs to plan-owned
- * device buffers, runs qst_forward and qst_adjoint on the stream, copies
+ * device buffers, runs qst_evaluate on the stream, copies
  * loss [1], grad_psi [K][D] complex64 and grad_w [K] back to the host buffers,
  * and synchronises the stream.  Every pointer here is host memory (pinned
  * memory gives asynchronous copies).  c_obs_out [nnz] may be NULL.

@@ -658,6 +658,7 @@ struct FwdArgs {
     int64_t src_bin_stride;  // elements between the sources of consecutive bins (0: all bins read psi)
     const int *skip;         // optional device flag: when set, the launch does nothing
     int n, r, K;
+    float2 *phi_obs = nullptr;  // optional [K][nnz]: the chunk transform of psi_k at the observed outcomes
 };
 
 // Forward unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -799,6 +800,8 @@ struct AdjArgs {
     float2 *zbuf;    // [bins][K][D]
     int64_t src_bin_stride;  // elements between the sources of consecutive bins (0: all bins read psi)
     int n, r, K;
+    const float2 *phi_obs = nullptr;  // [K][nnz] from the forward (the cached adjoint reads it instead of psi)
+    int64_t nnz = 0;
 };
 
 // Adjoint unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -995,6 +998,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_wide.cuh"
 #include "qst_fixed.cuh"
 #include "qst_tworound.cuh"
+#include "qst_tworound_packed.cuh"
 #include "qst_single.cuh"
 #include "qst_iterate.cuh"
 
@@ -1018,6 +1022,7 @@ struct qst_plan_s {
     bool wide = false;       // n = 17..20: high bits by butterfly passes, groups of wide_G settings
     bool fx = false;         // 12-qubit chunks with fixed-position rounds (k_forward_fx / k_adjoint_fx)
     bool fx2 = false;        // 12-qubit chunks in two 6-bit rounds, two atoms per CTA (k_forward_2r / k_adjoint_2r)
+    float2 *phi = nullptr;   // [K][nnz] transform cache of qst_evaluate (two-round plans, params.phi_cache)
     int wide_G = 0;
     float2 *wide_T = nullptr;    // [wide_G][K][D] intermediate (also the z buffer)
     double2 *wide_acc = nullptr; // [K][D] FP64 accumulator of G psi
@@ -1173,7 +1178,8 @@ void with_geo(int c, int ra, Fn &&fn) {
 // pair for the two-round kernels.
 void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t st) {
     if (p->fx2) {
-        k_forward_2r<<<units * ((p->K + 1) / 2), k2T, k2_smem(false).total, st>>>(a);
+        if (a.phi_obs) k_forward_2r<true><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
+        else k_forward_2r<false><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
         return;
     }
     const int grid = units * p->K;
@@ -1191,8 +1197,12 @@ void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t 
     });
 }
 void launch_adjoint_units(qst_plan p, const AdjArgs &a, int units, cudaStream_t st) {
+    if (p->fx2 && a.phi_obs) {
+        k_adjoint_2c<<<units * ((p->K + 1) / 2), k2T, k2c_smem().total, st>>>(a);
+        return;
+    }
     if (p->fx2) {
-        k_adjoint_2r<<<units * ((p->K + 1) / 2), k2T, k2_smem(true).total, st>>>(a);
+        k_adjoint_2r<<<units * ((p->K + 1) / 2), k2T, k2p_smem().total, st>>>(a);
         return;
     }
     const int grid = units * p->K;
@@ -1320,9 +1330,10 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
 
 qst_status forward_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const uint32_t *count, const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
-                        float *p_dense, const int *skip, cudaStream_t st);
+                        float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache = nullptr);
 qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
-                        const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st);
+                        const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st,
+                        const float2 *phi_cache = nullptr);
 }  // namespace
 
 extern "C" {
@@ -1336,6 +1347,7 @@ void qst_params_default(qst_params *p) {
     p->validate = 1;
     p->reg_bits = 0;
     p->fixed_rounds = -1;
+    p->phi_cache = -1;
 }
 
 const char *qst_status_string(qst_status s) {
@@ -1386,7 +1398,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
-    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 2) {
+    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 2 || prm.phi_cache < -1 || prm.phi_cache > 1) {
         delete p;
         return QST_ERR_INVALID_ARG;
     }
@@ -1412,6 +1424,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (p->smax >= 32 ? 2 : 1);
     p->fx2 = c == 12 && fr == 2 && !wide;
     p->fx = c == 12 && p->A == 4 && (fr == 1 || (fr == 2 && wide));
+    if (prm.phi_cache == 1 && !p->fx2) {  // the cached adjoint exists for the two-round kernels only
+        delete p;
+        return QST_ERR_UNSUPPORTED;
+    }
     const int64_t D = (int64_t)1 << n;
     if (wide) {
         p->wide = true;
@@ -1461,6 +1477,11 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         if (!rc) rc = dalloc(p, &p->lz_lam, kKrylovMax);
         if (!rc) rc = dalloc(p, &p->lz_int, 2);
     }
+    // qst_evaluate's transform cache: K x nnz complex values (1 GB for the
+    // n = 16, M = 4096, K = 16 workload); automatic for two-round plans up to 16 GiB
+    if (!rc && p->fx2 && nnz > 0 &&
+        (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30))))
+        rc = dalloc(p, &p->phi, (size_t)K * nnz);
     if (!rc) rc = dalloc(p, &p->it_state, 1);
     if (!rc && cudaMemset(p->it_state, 0, sizeof(IterState)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) rc = dalloc(p, &p->it_c, nnz);
@@ -1484,8 +1505,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_high_inv_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideInvSmem);
         }
         if (p->fx2) {
-            cudaFuncSetAttribute(k_forward_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(false).total);
-            cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem(true).total);
+            cudaFuncSetAttribute(k_forward_2r<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+            cudaFuncSetAttribute(k_forward_2r<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+            cudaFuncSetAttribute(k_adjoint_2c, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem().total);
+            cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
         }
         if (cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
     }
@@ -1499,6 +1522,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
 
 qst_status qst_plan_destroy(qst_plan p) {
     if (!p) return QST_ERR_INVALID_ARG;
+    cudaFree(p->phi);
     cudaFree(p->plans);
     cudaFree(p->order);
     cudaFree(p->bins);
@@ -1590,7 +1614,7 @@ namespace {
 // (optional) every launch returns at once.
 qst_status forward_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const uint32_t *count, const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
-                        float *p_dense, const int *skip, cudaStream_t st) {
+                        float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache) {
     qst_status rc = QST_OK;
     if (p_dense && cudaMemsetAsync(p_dense, 0, (size_t)p->M * ((size_t)1 << p->n) * sizeof(float), st) != cudaSuccess)
         return QST_ERR_CUDA;
@@ -1616,6 +1640,7 @@ qst_status forward_core(qst_plan p, const float *psi, const float *w, const int6
     a.K = p->K;
     a.src_bin_stride = 0;
     a.skip = skip;
+    a.phi_obs = phi_cache;
     const int units = p->nb_max << p->r;
     if (!p->wide) {
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
@@ -1657,7 +1682,8 @@ qst_status qst_adjoint(qst_plan p, const float *psi, const float *w, const uint8
 namespace {
 // The adjoint after packing and validation.
 qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
-                        const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st) {
+                        const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st,
+                        const float2 *phi_cache) {
     qst_status rc = QST_OK;
     AdjArgs a;
     a.psi = reinterpret_cast<const float2 *>(psi);
@@ -1674,6 +1700,8 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
     a.r = p->r;
     a.K = p->K;
     a.src_bin_stride = 0;
+    a.phi_obs = phi_cache;
+    a.nnz = p->nnz;
     if (p->wide) {
         rc = adjoint_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, c_obs,
                           reinterpret_cast<float2 *>(grad_psi), st);
@@ -1707,6 +1735,24 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
 }  // namespace
 
 extern "C" {
+
+qst_status qst_evaluate(qst_plan p, const float *psi, const float *w, const uint8_t *basis, const int64_t *row_ptr,
+                        const uint32_t *outcome, const uint32_t *count, const uint32_t *shots, float *p_obs,
+                        float *c_obs, double *loss, float *grad_psi, float *grad_w, void *stream) {
+    if (!p || !psi || !w || !basis || !row_ptr || !shots || !c_obs || !grad_psi) return QST_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!outcome || !count)) return QST_ERR_INVALID_ARG;
+    if (!aligned(psi, 16) || !aligned(grad_psi, 16) || !aligned(w, 4) || !aligned(row_ptr, 8) ||
+        (outcome && !aligned(outcome, 4)) || (count && !aligned(count, 4)) || !aligned(shots, 4) ||
+        (p_obs && !aligned(p_obs, 4)) || !aligned(c_obs, 4) || (loss && !aligned(loss, 8)) ||
+        (grad_w && !aligned(grad_w, 4)))
+        return QST_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    qst_status rc = prepare(p, basis, row_ptr, outcome, shots, st);
+    if (!rc) rc = forward_core(p, psi, w, row_ptr, outcome, count, shots, p_obs, c_obs, loss, nullptr, nullptr, st,
+                               p->phi);
+    if (!rc) rc = adjoint_core(p, psi, w, row_ptr, outcome, c_obs, grad_psi, grad_w, st, p->phi);
+    return rc;
+}
 
 qst_status qst_evaluate_host(qst_plan p, const float *psi, const float *w, const uint8_t *basis,
                              const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
@@ -1745,14 +1791,10 @@ qst_status qst_evaluate_host(qst_plan p, const float *psi, const float *w, const
 #undef QST_H2D
     const float *d_psi = (const float *)(base + o_psi);
     const float *d_w = (const float *)(base + o_w);
-    qst_status rc = qst_forward(p, d_psi, d_w, (const uint8_t *)(base + o_basis), (const int64_t *)(base + o_row),
-                                (const uint32_t *)(base + o_out), (const uint32_t *)(base + o_cnt),
-                                (const uint32_t *)(base + o_shots), nullptr, (float *)(base + o_c),
-                                (double *)(base + o_loss), nullptr, stream);
-    if (rc) return rc;
-    rc = qst_adjoint(p, d_psi, d_w, (const uint8_t *)(base + o_basis), (const int64_t *)(base + o_row),
-                     (const uint32_t *)(base + o_out), (const float *)(base + o_c), (float *)(base + o_grad),
-                     (float *)(base + o_gw), stream);
+    qst_status rc = qst_evaluate(p, d_psi, d_w, (const uint8_t *)(base + o_basis), (const int64_t *)(base + o_row),
+                                 (const uint32_t *)(base + o_out), (const uint32_t *)(base + o_cnt),
+                                 (const uint32_t *)(base + o_shots), nullptr, (float *)(base + o_c),
+                                 (double *)(base + o_loss), (float *)(base + o_grad), (float *)(base + o_gw), stream);
     if (rc) return rc;
     if (cudaMemcpyAsync(loss_out, base + o_loss, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return QST_ERR_CUDA;
     if (cudaMemcpyAsync(grad_psi_out, base + o_grad, b_psi, cudaMemcpyDeviceToHost, st) != cudaSuccess)

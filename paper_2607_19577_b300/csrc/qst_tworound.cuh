@@ -11,8 +11,10 @@
 // and the adjoint two (A -> B after the forward round A, B -> A before the
 // inverse round A), half of what three 4-bit rounds need.  A CTA runs two
 // atoms, k0 = 2 kp (warps 0-1) and k0 + 1 (warps 2-3), on the same bin and
-// high pattern: they share the staged setting metadata and the dense c
-// buffer, and the four warps reach all 128 TMEM lanes.
+// high pattern: they share the staged setting metadata (and, in the adjoint,
+// the dense c buffer), and the four warps reach all 128 TMEM lanes.  This file
+// holds the forward kernel on scalar complex registers; the adjoint kernel,
+// on packed FP32 pairs, is in qst_tworound_packed.cuh.
 //
 // Exchange buffer (one per atom): u at 66 hi + lo.  Round-A accesses (lanes
 // over lo) are contiguous; round-B accesses (lanes over hi, pairs of lo as
@@ -29,42 +31,32 @@ constexpr int k2Buf = 64 * k2Row;        // complex elements of one atom's excha
 constexpr int k2FRow = 68;               // floats per padded row of a float buffer
 constexpr int k2FBuf = 64 * k2FRow;      // floats of one float buffer
 constexpr int k2Stage = 512;             // observed entries per setting staged by cp.async
-constexpr uint32_t k2ColsFwd = 128, k2ColsAdj = 256;  // TMEM columns: source (+ accumulator)
+constexpr uint32_t k2ColsFwd = 128;     // TMEM columns of a forward CTA: the source
 
 __host__ __device__ constexpr uint32_t k2_fpos(uint32_t u) { return u + 4u * (u >> 6); }
 
 struct K2Smem {
     int work, fbuf, stage, masks, meta, tmem, total;
 };
-// fbuf: adjoint = two dense c buffers (settings alternate, shared by both
-// atoms); the forward writes w |.|^2 into each atom's exchange buffer once
-// the exchange is read, so it has no float buffer of its own
-__host__ __device__ constexpr K2Smem k2_smem(bool adjoint) {
+// The forward writes w |.|^2 into each atom's exchange buffer once the
+// exchange is read, so it has no float buffer of its own (fbuf = stage).
+__host__ __device__ constexpr K2Smem k2_smem_fwd() {
     K2Smem sp{};
     sp.work = 0;
     sp.fbuf = sp.work + 2 * k2Buf * 8;
-    sp.stage = sp.fbuf + (adjoint ? 2 * k2FBuf * 4 : 0);
-    sp.masks = sp.stage + 2 * k2Stage * (adjoint ? 8 : 4);
+    sp.stage = sp.fbuf;
+    sp.masks = sp.stage + 2 * k2Stage * 4;
     sp.meta = sp.masks + kMaxBin * (int)sizeof(uint2);
     sp.tmem = sp.meta + kMaxBin * (int)sizeof(SetMeta);
     sp.total = sp.tmem + 16;
     return sp;
 }
-static_assert(k2_smem(true).fbuf % 16 == 0 && k2_smem(true).stage % 16 == 0 && k2_smem(true).masks % 16 == 0 &&
-                  k2_smem(true).meta % 16 == 0,
-              "aligned shared arrays");
-static_assert(k2_smem(false).fbuf % 16 == 0 && k2_smem(false).masks % 16 == 0 && k2_smem(false).meta % 16 == 0,
+static_assert(k2_smem_fwd().fbuf % 16 == 0 && k2_smem_fwd().masks % 16 == 0 && k2_smem_fwd().meta % 16 == 0,
               "aligned shared arrays");
 static_assert(k2FBuf * 4 <= k2Buf * 8, "a float buffer fits in an exchange buffer");
 constexpr int k2SmemSM = 228 * 1024;  // shared memory per SM; each CTA also reserves 1 KB
-constexpr int k2CtaFwd = k2_smem(false).total + 1024, k2CtaAdj = k2_smem(true).total + 1024;
-static_assert(2 * k2CtaAdj <= k2SmemSM && 3 * k2CtaFwd <= k2SmemSM, "two adjoint or three forward CTAs per SM");
-// Shared memory admits at most two adjoint CTAs, three forward CTAs, or one
-// of each, on an SM; their TMEM columns then fit in the SM's 512, so an
-// allocation never waits.
-static_assert(3 * k2CtaAdj > k2SmemSM && 4 * k2CtaFwd > k2SmemSM && k2CtaAdj + 2 * k2CtaFwd > k2SmemSM &&
-                  2 * k2ColsAdj <= 512 && 3 * k2ColsFwd <= 512 && k2ColsAdj + k2ColsFwd <= 512,
-              "TMEM never oversubscribed");
+constexpr int k2CtaFwd = k2_smem_fwd().total + 1024;
+static_assert(3 * k2CtaFwd <= k2SmemSM && 4 * k2CtaFwd > k2SmemSM, "three forward CTAs per SM");
 
 // named barrier of the 64 threads of one atom (ids 1, 2; 0 is __syncthreads).
 // Immediate ids (half is warp-uniform) keep the CTA's barrier count at three.
@@ -125,30 +117,6 @@ __device__ __forceinline__ void k2_tm_st16(uint32_t taddr, const float2 (&v)[64]
     }
     tm_st(taddr + 32u * Q, r);
 }
-// z += v for the 128 accumulator columns, two 32-column blocks in flight.
-// The previous setting's stores to z complete first (their wait sits here,
-// so they drain during that setting's rounds).
-__device__ __forceinline__ void k2_tm_acc64(uint32_t taddr, const float2 (&v)[64]) {
-    tm_wait_st();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t r0[32], r1[32];
-        tm_ld_issue(taddr + 64u * h, r0);
-        tm_ld_issue(taddr + 64u * h + 32u, r1);
-        tm_ld_wait(r0);
-        tm_ld_wait(r1);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            r0[2 * i] = __float_as_uint(__uint_as_float(r0[2 * i]) + v[32 * h + i].x);
-            r0[2 * i + 1] = __float_as_uint(__uint_as_float(r0[2 * i + 1]) + v[32 * h + i].y);
-            r1[2 * i] = __float_as_uint(__uint_as_float(r1[2 * i]) + v[32 * h + 16 + i].x);
-            r1[2 * i + 1] = __float_as_uint(__uint_as_float(r1[2 * i + 1]) + v[32 * h + 16 + i].y);
-        }
-        tm_st(taddr + 64u * h, r0);
-        tm_st(taddr + 64u * h + 32u, r1);
-    }
-}
-
 // Chunk f of (U_h (x) I) psi_k in round A's layout (element i of thread t =
 // amplitude t + 64 i) -> TMEM columns 0..127, built 16 elements at a time.
 // An inactive atom (k >= K) gets zeros.
@@ -209,17 +177,13 @@ __device__ __forceinline__ void butterfly_herm(float2 (&v)[1 << A], uint32_t xyf
     }
 }
 
-// Exchanges.  Round A -> B: element i of thread t (= lo) goes to 66 i + t;
-// round B reads elements 2 jj, 2 jj + 1 of thread t (= hi) at 66 t + 2 jj as
-// one float4.  B -> A is the reverse.  A thread's round-A addresses are the
-// same in both directions, and so are its round-B addresses.
+// Exchange A -> B: element i of thread t (= lo) goes to 66 i + t; round B
+// reads elements 2 jj, 2 jj + 1 of thread t (= hi) at 66 t + 2 jj as one
+// float4; the cached forward writes its round-B values back to the same
+// positions (each thread overwrites only its own row).
 __device__ __forceinline__ void k2_store_A(const float2 (&v)[64], float2 *wk, uint32_t t) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) wk[k2Row * i + t] = v[i];
-}
-__device__ __forceinline__ void k2_load_A(float2 (&v)[64], const float2 *wk, uint32_t t) {
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = wk[k2Row * i + t];
 }
 __device__ __forceinline__ void k2_store_B(const float2 (&v)[64], float2 *wk, uint32_t t) {
     float4 *w4 = reinterpret_cast<float4 *>(wk + k2Row * t);
@@ -245,8 +209,14 @@ __device__ __forceinline__ void k2_load_B(float2 (&v)[64], const float2 *wk, uin
 // block barrier (the staged outcomes) and three barriers of the atom's 64
 // threads (the exchange, buffer reuse before the float writes, and the
 // gather before the next setting's exchange).
+//
+// CACHE (the evaluate path): the round-B values stay in the exchange buffer as
+// complex numbers instead (each thread rewrites only its own row, which only
+// it read), and the gather also stores them, unscaled, at the observed
+// outcomes into the atom's slice of a.phi_obs, for the cached adjoint.
+template <bool CACHE>
 __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
-    constexpr K2Smem sp = k2_smem(false);
+    constexpr K2Smem sp = k2_smem_fwd();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem + sp.stage);
     uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);
@@ -307,17 +277,21 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
                 k2_load_B(v, wk, t);
             }
         }
-        k2_bar_atom(half);  // every round-B read of the exchange buffer is done
         const float sc = wkk * mt.cs;
-        float4 *p4 = reinterpret_cast<float4 *>(pb + k2FRow * t);
+        if (CACHE) {
+            k2_store_B(v, wk, t);
+        } else {
+            k2_bar_atom(half);  // every round-B read of the exchange buffer is done
+            float4 *p4 = reinterpret_cast<float4 *>(pb + k2FRow * t);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            float4 o;
-            o.x = sc * (v[4 * q].x * v[4 * q].x + v[4 * q].y * v[4 * q].y);
-            o.y = sc * (v[4 * q + 1].x * v[4 * q + 1].x + v[4 * q + 1].y * v[4 * q + 1].y);
-            o.z = sc * (v[4 * q + 2].x * v[4 * q + 2].x + v[4 * q + 2].y * v[4 * q + 2].y);
-            o.w = sc * (v[4 * q + 3].x * v[4 * q + 3].x + v[4 * q + 3].y * v[4 * q + 3].y);
-            p4[q] = o;
+            for (int q = 0; q < 16; ++q) {
+                float4 o;
+                o.x = sc * (v[4 * q].x * v[4 * q].x + v[4 * q].y * v[4 * q].y);
+                o.y = sc * (v[4 * q + 1].x * v[4 * q + 1].x + v[4 * q + 1].y * v[4 * q + 1].y);
+                o.z = sc * (v[4 * q + 2].x * v[4 * q + 2].x + v[4 * q + 2].y * v[4 * q + 2].y);
+                o.w = sc * (v[4 * q + 3].x * v[4 * q + 3].x + v[4 * q + 3].y * v[4 * q + 3].y);
+                p4[q] = o;
+            }
         }
         cp_async_wait0();
         __syncthreads();  // this setting's stage landed (every thread's copies); the floats are written
@@ -325,7 +299,23 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
         // which every thread finished before the barrier above
         issue(si + 1);
         const uint32_t *st = stage + (si & 1) * k2Stage;
-        if (active) {
+        if (active && CACHE) {
+            float2 *phk = a.phi_obs + (size_t)k * a.nnz;
+            for (int j = t; j < mt.cnt; j += 64) {
+                const uint32_t u = (j < k2Stage ? st[j] : outcome[mt.lo + j]) & cmask;
+                const float2 ph = wk[k2Row * (u >> 6) + (u & 63u)];
+                pk[mt.lo + j] = sc * (ph.x * ph.x + ph.y * ph.y);
+                phk[mt.lo + j] = ph;
+            }
+            if (a.p_dense) {
+                const int s = a.order[b.start + si];
+                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << 12);
+                for (uint32_t u = t; u <= cmask; u += 64) {
+                    const float2 ph = wk[k2Row * (u >> 6) + (u & 63u)];
+                    atomicAdd(pd + u, sc * (ph.x * ph.x + ph.y * ph.y));
+                }
+            }
+        } else if (active) {
             for (int j = t; j < mt.cnt; j += 64) {
                 const uint32_t u = (j < k2Stage ? st[j] : outcome[mt.lo + j]) & cmask;
                 pk[mt.lo + j] = pb[k2_fpos(u)];
@@ -347,144 +337,3 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
     }
 }
 
-// Adjoint CTA = (bin, high pattern f, atom pair kp).  Per setting: round A,
-// exchange, round B, the c multiply, inverse round B, exchange, inverse round
-// A, and z += v in TMEM (round A's layout).  Two block barriers per setting,
-// one in each exchange; they also order the dense c buffers:
-//   * setting si reads c buffer si mod 2 between its two barriers;
-//   * after the second barrier a thread clears the entries of setting si it
-//     scattered itself, then scatters setting si + 1 into the other buffer,
-//     whose entries of setting si - 1 were cleared before this setting's
-//     first barrier, and which setting si + 1 reads after its first barrier.
-// A thread's round-A (round-B) exchange addresses are the same in both
-// directions, so it only overwrites addresses that it has read itself.
-__global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
-    constexpr K2Smem sp = k2_smem(true);
-    extern __shared__ __align__(16) unsigned char smem[];
-    float *cbuf = reinterpret_cast<float *>(smem + sp.fbuf);
-    uint32_t *stage_u = reinterpret_cast<uint32_t *>(smem + sp.stage);
-    float *stage_c = reinterpret_cast<float *>(smem + sp.stage + 2 * k2Stage * 4);
-    uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);
-    SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
-    uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
-    const int KP = (a.K + 1) >> 1;
-    const int unit = blockIdx.x;
-    const int kp = unit % KP;
-    const int rest = unit / KP;
-    const uint32_t f = rest & ((1u << a.r) - 1u);
-    const int bin = rest >> a.r;
-    if (bin >= *a.n_bins) return;
-    const Bin b = a.bins[bin];
-    const int D = 1 << a.n;
-    const int k = 2 * kp + (int)half;
-    const bool active = k < a.K;
-    float2 *wk = reinterpret_cast<float2 *>(smem + sp.work) + half * k2Buf;
-    constexpr uint32_t cmask = 4095u;
-    if (warp == 0) tm_alloc(tmem_sm, k2ColsAdj);
-    for (int u = tid; u < 2 * k2FBuf; u += k2T) cbuf[u] = 0.f;
-    fx_stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, masks_sm, meta_sm);
-    tm_fence_before();
-    __syncthreads();
-    tm_fence_after();
-    const uint32_t t_src = tmem_sm[0] + ((warp * 32u) << 16);
-    const uint32_t t_z = t_src + 128u;
-    const int bcount = b.count;
-    const uint32_t *outcome = a.outcome;
-    const float *c_obs = a.c_obs;
-    auto issue = [=](int si) {
-        if (si < bcount) {
-            const SetMeta mt = meta_sm[si];
-            const int nst = mt.cnt < k2Stage ? mt.cnt : k2Stage;
-            uint32_t *du = stage_u + (si & 1) * k2Stage;
-            float *dc = stage_c + (si & 1) * k2Stage;
-            for (int j = tid; j < nst; j += k2T) {
-                cp_async4(du + j, outcome + mt.lo + j);
-                cp_async4(dc + j, c_obs + mt.lo + j);
-            }
-        }
-        cp_async_commit();
-    };
-    // scatter c 2^-m of setting si into c buffer si mod 2, or clear those
-    // entries; each thread touches the entries it staged itself
-    auto scatter = [=](int si, bool clear) {
-        const SetMeta mt = meta_sm[si];
-        const uint32_t *su = stage_u + (si & 1) * k2Stage;
-        const float *sc = stage_c + (si & 1) * k2Stage;
-        float *cb = cbuf + (si & 1) * k2FBuf;
-        for (int j = tid; j < mt.cnt; j += k2T) {
-            const bool st = j < k2Stage;
-            const uint32_t u = (st ? su[j] : outcome[mt.lo + j]) & cmask;
-            cb[k2_fpos(u)] = clear ? 0.f : (st ? sc[j] : c_obs[mt.lo + j]) * mt.cs;
-        }
-    };
-    issue(0);
-    k2_build_source(t_src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)(active ? k : 0) * D, active, f, b.xytop,
-                    b.ytop, t);
-    {
-        const float2 zero[64] = {};
-        k2_tm_st16<0>(t_z, zero);
-        k2_tm_st16<1>(t_z, zero);
-        k2_tm_st16<2>(t_z, zero);
-        k2_tm_st16<3>(t_z, zero);
-    }
-    tm_wait_st();
-    cp_async_wait0();
-    if (bcount > 0) scatter(0, false);  // the c buffers were zeroed before the barrier above
-    issue(1);
-    float2 v[64];
-    for (int si = 0; si < bcount; ++si) {
-        const uint2 mk = masks_sm[si];
-        k2_tm_ld64(t_src, v);
-        // the four rounds (A, B, then B, A conjugate-transposed = the same
-        // Hermitian factors) share one butterfly site; between them: the
-        // exchange A -> B, the c multiply, the exchange B -> A
-#pragma unroll 1
-        for (int ph = 0; ph < 4; ++ph) {
-            const uint32_t sh = (ph == 0 || ph == 3) ? 6u : 0u;
-            butterfly_herm<6>(v, (mk.x >> sh) & 63u, (mk.y >> sh) & 63u);
-            if (ph == 0) {
-                k2_store_A(v, wk, t);
-                __syncthreads();
-                k2_load_B(v, wk, t);
-            } else if (ph == 1) {
-                const float4 *c4 = reinterpret_cast<const float4 *>(cbuf + (si & 1) * k2FBuf + k2FRow * t);
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 cc = c4[q];
-                    v[4 * q].x *= cc.x;
-                    v[4 * q].y *= cc.x;
-                    v[4 * q + 1].x *= cc.y;
-                    v[4 * q + 1].y *= cc.y;
-                    v[4 * q + 2].x *= cc.z;
-                    v[4 * q + 2].y *= cc.z;
-                    v[4 * q + 3].x *= cc.w;
-                    v[4 * q + 3].y *= cc.w;
-                }
-            } else if (ph == 2) {
-                k2_store_B(v, wk, t);
-                __syncthreads();
-                k2_load_A(v, wk, t);
-            }
-        }
-        k2_tm_acc64(t_z, v);
-        scatter(si, true);
-        cp_async_wait0();
-        if (si + 1 < bcount) scatter(si + 1, false);
-        issue(si + 2);
-    }
-    cp_async_wait0();
-    tm_wait_st();
-    if (active) {
-        k2_tm_ld64(t_z, v);
-        float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << 12);
-#pragma unroll
-        for (int i = 0; i < 64; ++i) zo[t + 64u * i] = v[i];
-    }
-    tm_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tm_fence_after();
-        tm_dealloc(tmem_sm[0], k2ColsAdj);
-    }
-}

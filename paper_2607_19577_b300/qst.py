@@ -38,7 +38,8 @@ class QSTError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm_settings", ctypes.c_int),
                 ("chunk_qubits", ctypes.c_int), ("max_bin_settings", ctypes.c_int),
-                ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int), ("fixed_rounds", ctypes.c_int)]
+                ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int), ("fixed_rounds", ctypes.c_int),
+                ("phi_cache", ctypes.c_int)]
 
 
 class _StepParams(ctypes.Structure):
@@ -77,6 +78,7 @@ def load():
         lib.qst_forward.argtypes = [P] + [P] * 11 + [P]
         lib.qst_adjoint.argtypes = [P] + [P] * 8 + [P]
         lib.qst_evaluate_host.argtypes = [P] + [P] * 11 + [P]
+        lib.qst_evaluate.argtypes = [P] + [P] * 12 + [P]
         lib.qst_plan_status.argtypes = [P, ctypes.POINTER(i32)]
         lib.qst_plan_set_timing.argtypes = [P, i32]
         lib.qst_plan_kernel_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(f64), i32]
@@ -94,7 +96,7 @@ def load():
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
                                  ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
         for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_tangent", "qst_iterate", "qst_forward",
-                     "qst_adjoint", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
+                     "qst_adjoint", "qst_evaluate", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
                      "qst_batch_create", "qst_batch_destroy", "qst_batch_plan", "qst_batch_evaluate"]:
@@ -156,7 +158,7 @@ class Plan:
     """Owns a qst_plan (device workspace for one problem shape)."""
 
     def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
-                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=-1):
+                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=-1, phi_cache=-1):
         lib = load()
         prm = _Params()
         lib.qst_params_default(ctypes.byref(prm))
@@ -165,6 +167,8 @@ class Plan:
         # fixed_rounds (12-qubit chunks): 2 = two 6-qubit rounds, 1 = three 4-qubit
         # rounds, 0 = per-setting rounds, -1 = automatic (True / False mean 1 / 0)
         prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(fixed_rounds)
+        # phi_cache: qst_evaluate's transform cache (two-round plans): 1 on, 0 off, -1 automatic
+        prm.phi_cache = int(phi_cache)
         h = ctypes.c_void_p()
         _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
                "qst_plan_create")
@@ -243,6 +247,29 @@ class Plan:
                                 _ptr(d.outcome), _ptr(c_obs), _ptr(grad_psi), _ptr(grad_w), _stream())
         _check(rc, "qst_adjoint")
         return grad_psi, grad_w
+
+    def evaluate(self, psi, w, d: Data, p_obs=None, c_obs=None, loss=None, grad_psi=None, grad_w=None):
+        """Runs qst_evaluate (forward, then the adjoint with the forward's c, using the
+        plan's transform cache when it has one); returns (p_obs, c_obs, loss, grad_psi, grad_w)."""
+        _need(psi, torch.complex64, (self.K, self.D), "psi")
+        _need(w, torch.float32, (self.K,), "w")
+        self._data(d)
+        dev = psi.device
+        p_obs = torch.empty(self.nnz, dtype=torch.float32, device=dev) if p_obs is None else p_obs
+        c_obs = torch.empty(self.nnz, dtype=torch.float32, device=dev) if c_obs is None else c_obs
+        loss = torch.empty(1, dtype=torch.float64, device=dev) if loss is None else loss
+        grad_psi = torch.empty_like(psi) if grad_psi is None else grad_psi
+        grad_w = torch.empty_like(w) if grad_w is None else grad_w
+        _need(p_obs, torch.float32, (self.nnz,), "p_obs")
+        _need(c_obs, torch.float32, (self.nnz,), "c_obs")
+        _need(loss, torch.float64, (1,), "loss")
+        _need(grad_psi, torch.complex64, (self.K, self.D), "grad_psi")
+        _need(grad_w, torch.float32, (self.K,), "grad_w")
+        rc = load().qst_evaluate(self._h, _ptr(psi), _ptr(w), _ptr(d.basis), _ptr(d.row_ptr), _ptr(d.outcome),
+                                 _ptr(d.count), _ptr(d.shots), _ptr(p_obs), _ptr(c_obs), _ptr(loss), _ptr(grad_psi),
+                                 _ptr(grad_w), _stream())
+        _check(rc, "qst_evaluate")
+        return p_obs, c_obs, loss, grad_psi, grad_w
 
     def evaluate_host(self, psi, w, basis, row_ptr, outcome, count, shots, stream=None):
         """Forward + adjoint from host numpy arrays (copies inside the call).

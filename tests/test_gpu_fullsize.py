@@ -173,3 +173,14 @@ def test_all_settings_adjoint_k2(c3k2):
         err = np.max(np.abs(c3k2["g"][k] - ref["grad_psi"][k])) / nrm
         assert err <= G_TOL, (k, err)
     np.testing.assert_allclose(c3k2["gw"], ref["grad_w"], rtol=H_TOL)
+
+
+def test_evaluate_equals_forward_then_adjoint_at_full_size(c3):
+    """qst_evaluate in the bench's configuration (transform cache on) gives the
+    bits of qst_forward + qst_adjoint on the whole n = 16, M = 4096, K = 16 workload."""
+    p_obs, c_obs, loss, g, gw = c3["plan"].evaluate(c3["psi"], c3["w"], c3["data"])
+    torch.cuda.synchronize()
+    assert c3["plan"].status() == 0
+    assert torch.equal(p_obs, c3["p_obs"]) and torch.equal(c_obs, c3["c_obs"])
+    assert loss.item() == c3["loss"].item()
+    assert torch.equal(g, c3["g"]) and torch.equal(gw, c3["gw"])

@@ -318,3 +318,50 @@ def test_tangent_matches_oracle(n, M, K, seed):
     t2 = plan.tangent(tp, tw, g, gw, out=g).cpu().numpy().astype(np.complex128)
     np.testing.assert_array_equal(t2, t)
     plan.close()
+
+
+def run_gpu_evaluate(inst, **plan_kw):
+    """qst_evaluate (forward, then the adjoint with the transform cache when the
+    plan has one) -> the same dict as run_gpu."""
+    plan = qst.Plan(inst.n, inst.M, inst.K, inst.nnz, eps=inst.eps, **plan_kw)
+    data = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    psi = torch.from_numpy(inst.psi).cuda()
+    w = torch.from_numpy(inst.w).cuda()
+    p_obs, c_obs, loss, g, gw = plan.evaluate(psi, w, data)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    out = dict(p_obs=p_obs.cpu().numpy().astype(np.float64), c_obs=c_obs.cpu().numpy().astype(np.float64),
+               loss=float(loss.item()), grad_psi=g.cpu().numpy().astype(np.complex128),
+               grad_w=gw.cpu().numpy().astype(np.float64))
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("n,M,K,smax,seed", [(12, 40, 3, 0, 0), (13, 31, 2, 7, 1), (14, 45, 5, 96, 2),
+                                              (16, 9, 1, 2, 3), (16, 14, 4, 0, 4)])
+def test_evaluate_with_transform_cache_matches_oracle(n, M, K, smax, seed):
+    """qst_evaluate on two-round plans (transform cache on: the adjoint applies only
+    the inverse rounds to c .* the stored transforms) against the oracle, and
+    bitwise equal to qst_forward + qst_adjoint (the same arithmetic in another
+    order of launches); odd K leaves the last CTA's second atom idle."""
+    inst = synth.random_instance(n, M, K, 700, 1400 + seed)
+    kw = dict(fixed_rounds=2, max_bin_settings=smax, phi_cache=1)
+    ev = run_gpu_evaluate(inst, **kw)
+    compare(inst, ev, run_oracle(inst))
+    sep = run_gpu(inst, **kw)
+    for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
+        assert np.array_equal(ev[key], sep[key]), key
+    assert ev["loss"] == sep["loss"]
+
+
+def test_evaluate_without_cache_and_other_families():
+    """Without the cache (or on plans whose kernels have no cached adjoint)
+    qst_evaluate is qst_forward + qst_adjoint."""
+    inst = synth.random_instance(13, 20, 3, 600, 1450)
+    for kw in (dict(fixed_rounds=2, phi_cache=0), dict(fixed_rounds=1), dict(fixed_rounds=0)):
+        ev = run_gpu_evaluate(inst, **kw)
+        sep = run_gpu(inst, **kw)
+        for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
+            assert np.array_equal(ev[key], sep[key]), (kw, key)
+    with pytest.raises(qst.QSTError):
+        qst.Plan(inst.n, inst.M, inst.K, inst.nnz, fixed_rounds=1, phi_cache=1)
