@@ -1,7 +1,9 @@
 #!/usr/bin/env python
 """Benchmark: one step = forward + adjoint over one batch of synthetic data
 (n = 16 qubits, M = 4096 random Pauli settings, 2000 shots each, K = 16 atoms),
-through the C ABI of libqst.so.
+through the C ABI of libqst.so (qst_evaluate: the forward stores the rotated
+amplitudes at the observed outcomes and the adjoint applies the inverse
+rotations to them; the line also records the adjoint that recomputes them).
 
 Prints ONE JSON line (rank 0).  Timing: W untimed warm-up steps, then K steps
 bracketed by a barrier + device synchronisation; each step is timed with CUDA
@@ -53,6 +55,9 @@ def parse_args():
     ap.add_argument("--no-iterations", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance batched evaluation (field batched; single rank only)")
+    ap.add_argument("--phi-cache", type=int, default=-1, choices=[-1, 0, 1],
+                    help="qst_evaluate's transform cache: 1 on, 0 off (the adjoint recomputes the rotations), "
+                         "-1 the plan's automatic choice")
     ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="12-qubit chunk kernels: 2 = two 6-qubit rounds, 1 = three 4-qubit rounds, "
                          "0 = rounds chosen per setting, -1 = the plan's automatic choice")
@@ -133,12 +138,18 @@ def kernel_source_hash():
 
 
 def algorithmic_ops(basis, K, D):
-    """FP32 lane operations (FADD/FMUL/FFMA each 1) of the plain butterfly method:
-    forward 2 m_s + 4 and adjoint 4 m_s + 8 per amplitude, m_s = X/Y qubits of s."""
+    """FP32 lane operations (FADD/FMUL/FFMA each 1) of the plain butterfly method,
+    per amplitude with m_s = X/Y qubits of setting s: the forward rotation and
+    |.|^2 weighting 2 m_s + 4; the adjoint 4 m_s + 8 when it recomputes the
+    rotation (2 m_s + 4 for the recomputation, 2 m_s + 4 for the inverse rotation,
+    c scaling and accumulation).  Returns (forward, recomputing adjoint, inverse
+    part alone), the last being the work of the adjoint that reads the stored
+    transforms."""
     m = np.count_nonzero(basis, axis=1).astype(np.float64)
     fwd = float(np.sum(2 * m + 4)) * K * D
     adj = float(np.sum(4 * m + 8)) * K * D
-    return fwd, adj
+    inv = float(np.sum(2 * m + 4)) * K * D
+    return fwd, adj, inv
 
 
 def cpu_oracle_rate(inst, budget_s, settings_per_call=1, max_settings=None):
@@ -311,7 +322,7 @@ def run_ours(args):
         args.fixed_rounds = best["fixed_rounds"]
         tuned = [{"params": p, "ms": t} for p, t in table]
     plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
-                    max_bin_settings=args.max_bin_settings, fixed_rounds=args.fixed_rounds)
+                    max_bin_settings=args.max_bin_settings, fixed_rounds=args.fixed_rounds, phi_cache=args.phi_cache)
     p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
     c_obs = torch.empty_like(p_obs)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -321,10 +332,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        plan.forward(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss)
-        plan.adjoint(psi, w, data, c_obs, grad_psi=grad, grad_w=grad_w)
+        plan.evaluate(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss, grad_psi=grad, grad_w=grad_w)
 
     for _ in range(max(args.warmup, 0)):
+        flush.zero_()  # the first fill also loads torch's kernel (about 0.3 s): keep it out of the timed loop
         step()
     torch.cuda.synchronize()
     plan.check()
@@ -359,9 +370,10 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     value = amps_all / (ms_step / 1e3)
 
-    # roofline of the dominant kernel (the adjoint)
-    fwd_ops, adj_ops = algorithmic_ops(inst.basis, K, D)
+    # roofline of the dominant kernel
+    fwd_ops, adj_ops, inv_ops = algorithmic_ops(inst.basis, K, D)
     geo = plan.geometry()
+    cached = geo["fixed_rounds"] == 2 and args.phi_cache != 0
     # per-step kernel time (the wide path launches its chunk kernels once per setting group)
     la, ms_adj = stats["adjoint"]
     lf, ms_fwd = stats["forward"]
@@ -374,8 +386,10 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_alu = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # TFLOP/s, 1 per lane-op
-    achieved = adj_ops / (adj_ms / 1e3) / 1e12
-    adj_kernel = {2: "k_adjoint_2r", 1: "k_adjoint_fx"}.get(geo["fixed_rounds"], "k_adjoint")
+    adj_work = inv_ops if cached else adj_ops  # the adjoint kernel's own algorithmic work
+    achieved = adj_work / (adj_ms / 1e3) / 1e12
+    adj_kernel = ("k_adjoint_2c" if cached else
+                  {2: "k_adjoint_2r", 1: "k_adjoint_fx"}.get(geo["fixed_rounds"], "k_adjoint"))
     traffic = None
     prof = os.path.join(ROOT, "profiles", "adjoint_traffic.json")
     if os.path.exists(prof):
@@ -392,11 +406,52 @@ def run_ours(args):
                 "kernel": adj_kernel,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                "(max SM clock of MEASURED_PEAKS.json)",
-                "ops_per_launch": adj_ops, "ms_per_launch": adj_ms,
+                "ops_per_launch": adj_work, "ms_per_launch": adj_ms,
+                "ops_definition": ("inverse rotation, c scaling, accumulation: 2 m_s + 4 FP32 lane-ops per "
+                                   "amplitude (the adjoint reads the forward's stored transforms)" if cached else
+                                   "recomputed rotation + inverse rotation: 4 m_s + 8 FP32 lane-ops per amplitude"),
                 "launches_per_step": la / args.steps,
-                "forward": {"ops_per_launch": fwd_ops, "ms_per_launch": ms_fwd / args.steps,
-                            "achieved": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12}}
+                "forward": {"kernel": "k_forward_2r" if geo["fixed_rounds"] == 2 else "forward",
+                            "ops_per_launch": fwd_ops, "ms_per_launch": ms_fwd / args.steps,
+                            "achieved": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12,
+                            "frac": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12 / peak_alu},
+                "step_vs_plain_path": {
+                    "ops_per_step": fwd_ops + adj_ops, "ms_per_step": ms_step,
+                    "frac": (fwd_ops + adj_ops) / (ms_step / 1e3) / 1e12 / peak_alu,
+                    "definition": "the plain FP32 method's work for one forward + recomputing adjoint "
+                                  "(6 m_s + 12 lane-ops per amplitude) at the FP32 lane peak, over the whole "
+                                  "step's time"}}
     kern = {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}
+
+    # the same evaluation through qst_forward + qst_adjoint, whose adjoint
+    # recomputes the rotations (the plain path's structure), for its roofline
+    recompute = None
+    if cached:
+        def sep():
+            plan.forward(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss)
+            plan.adjoint(psi, w, data, c_obs, grad_psi=grad, grad_w=grad_w)
+        for _ in range(2):
+            flush.zero_()
+            sep()
+        torch.cuda.synchronize()
+        plan.set_timing(True)
+        plan.reset_stats()
+        reps = max(3, min(args.steps, 10))
+        for _ in range(reps):
+            flush.zero_()
+            sep()
+        torch.cuda.synchronize()
+        rs = plan.kernel_stats()
+        plan.set_timing(False)
+        r_adj = rs["adjoint"][1] / reps
+        recompute = {"kernel": "k_adjoint_2r", "ops_per_launch": adj_ops, "ms_per_launch": r_adj,
+                     "achieved": adj_ops / (r_adj / 1e3) / 1e12,
+                     "frac": adj_ops / (r_adj / 1e3) / 1e12 / peak_alu,
+                     "forward_ms": rs["forward"][1] / reps,
+                     "ms_per_step": sum(v[1] for v in rs.values()) / reps,
+                     "how": "qst_forward + qst_adjoint (the adjoint recomputes V_s psi_k), per-launch events, "
+                            f"{reps} steps, L2 flushed between steps"}
+        roofline["recompute_path"] = recompute
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
@@ -473,6 +528,9 @@ def run_ours(args):
                 "data": "synthetic (seeded; Pauli strings uniform, Porter-Thomas surrogate counts)",
                 "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
                            "nnz": int(inst.nnz), "precision_path": "plain FP32",
+                           "step": "qst_evaluate: forward (stores the chunk transforms at the observed outcomes) + "
+                                   "adjoint (inverse rotations of c .* the stored transforms)" if cached else
+                                   "qst_evaluate: forward + adjoint that recomputes the rotations",
                            "plan": {"reg_bits": args.reg_bits, "chunk_qubits": args.chunk_qubits,
                                     "max_bin_settings": args.max_bin_settings,
                                     "geometry": geo, "autotune": tuned},
