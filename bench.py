@@ -55,6 +55,10 @@ def parse_args():
     ap.add_argument("--no-iterations", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance batched evaluation (field batched; single rank only)")
+    ap.add_argument("--shard", action="store_true",
+                    help="each rank evaluates a contiguous shard of the settings with the global B and the ranks "
+                         "all-reduce (loss, grad, grad_w) every step (measurement partition of Sec. III-B); "
+                         "the default runs one replica per rank")
     ap.add_argument("--phi-cache", type=int, default=-1, choices=[-1, 0, 1],
                     help="qst_evaluate's transform cache: 1 on, 0 off (the adjoint recomputes the rotations), "
                          "-1 the plan's automatic choice")
@@ -310,6 +314,15 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     inst = synth.make_instance(args.workload, seed=0)
+    M_all = inst.M
+    if args.shard:
+        # this rank's contiguous range of the settings, evaluated with the global B
+        # (the measurement partition of Sec. III-B); the sums are all-reduced per step
+        lo, hi = replicas.shard(M_all, rank, ws)
+        rp, ea, eb = replicas.shard_rows(inst.row_ptr, lo, hi)
+        inst = synth.Instance(name=inst.name, n=inst.n, basis=inst.basis[lo:hi], shots=inst.shots[lo:hi],
+                              row_ptr=rp, outcome=inst.outcome[ea:eb], count=inst.count[ea:eb], psi=inst.psi,
+                              w=inst.w)
     n, M, K, D = inst.n, inst.M, inst.K, inst.D
     data = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
     psi = torch.from_numpy(inst.psi).cuda()
@@ -322,7 +335,8 @@ def run_ours(args):
         args.fixed_rounds = best["fixed_rounds"]
         tuned = [{"params": p, "ms": t} for p, t in table]
     plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
-                    max_bin_settings=args.max_bin_settings, fixed_rounds=args.fixed_rounds, phi_cache=args.phi_cache)
+                    max_bin_settings=args.max_bin_settings, fixed_rounds=args.fixed_rounds, phi_cache=args.phi_cache,
+                    norm_settings=M_all if args.shard else 0)
     p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
     c_obs = torch.empty_like(p_obs)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -333,6 +347,8 @@ def run_ours(args):
 
     def step():
         plan.evaluate(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss, grad_psi=grad, grad_w=grad_w)
+        if args.shard:
+            replicas.allreduce_evaluation(loss, grad, grad_w, dist)
 
     for _ in range(max(args.warmup, 0)):
         flush.zero_()  # the first fill also loads torch's kernel (about 0.3 s): keep it out of the timed loop
@@ -365,7 +381,8 @@ def run_ours(args):
     plan.check()
     ms_total = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     amps_step = M * K * D
-    # slowest rank's time, every rank's units (each rank runs one replica)
+    # slowest rank's time, every rank's units (each rank runs one replica, or one
+    # shard of the settings: then the units add up to the one experiment's M K D)
     ms_total, amps_all = replicas.aggregate(ms_total, amps_step, dist, device="cuda")
     ms_step = ms_total / args.steps
     value = amps_all / (ms_step / 1e3)
@@ -426,7 +443,7 @@ def run_ours(args):
     # the same evaluation through qst_forward + qst_adjoint, whose adjoint
     # recomputes the rotations (the plain path's structure), for its roofline
     recompute = None
-    if cached:
+    if cached and not args.shard:
         def sep():
             plan.forward(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss)
             plan.adjoint(psi, w, data, c_obs, grad_psi=grad, grad_w=grad_w)
@@ -455,7 +472,7 @@ def run_ours(args):
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.shard:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         h_psi = torch.from_numpy(inst.psi.view(np.float32)).pin_memory().numpy().view(np.complex64)
         h = [pin(inst.w), pin(inst.basis), pin(inst.row_ptr), pin(inst.outcome), pin(inst.count), pin(inst.shots)]
@@ -483,7 +500,7 @@ def run_ours(args):
     # Algorithm 1 iterations on the device (qst_iterate: one CUDA graph, atom /
     # coefficient slots of the Table I schedule), timed with CUDA events
     algo = None
-    if not args.no_iterations:
+    if not args.no_iterations and not args.shard:
         it_T = args.iterations
         ip_psi, ip_w = psi.clone(), w.clone()
         Jh, acc = plan.iterate(it_T, 0, ip_psi, ip_w, data)  # capture + first run (untimed)
@@ -505,7 +522,7 @@ def run_ours(args):
                        "from the bench state"}
 
     batched = None
-    if ws == 1 and not args.no_batched:
+    if ws == 1 and not args.no_batched and not args.shard:
         batched = batched_eval(flush)
 
     cpu = None
@@ -524,7 +541,8 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "s_per_iteration": ms_step / 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
+                "dtype": "f32",
                 "data": "synthetic (seeded; Pauli strings uniform, Porter-Thomas surrogate counts)",
                 "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
                            "nnz": int(inst.nnz), "precision_path": "plain FP32",
@@ -535,7 +553,8 @@ def run_ours(args):
                                     "max_bin_settings": args.max_bin_settings,
                                     "geometry": geo, "autotune": tuned},
                            "l2": "flushed between timed steps (512 MiB write outside the events)",
-                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                           "parallelism": (f"setting shards over {ws} ranks + all-reduce of (loss, grad, grad_w)"
+                                           if args.shard else ("replicas" if ws > 1 else "single GPU"))},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "algorithm1": algo, "batched": batched,
                 "gpu_launches": launches, "kernels": kern, "wall_ms_per_step": 1e3 * t_wall / args.steps,

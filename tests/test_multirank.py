@@ -31,20 +31,26 @@ def _worker(rank, world, port):
         psi = inst.psi.astype(np.complex128)
         w = inst.w.astype(np.float64)
         lo, hi = replicas.shard(M, rank, world)
-        a, b = inst.row_ptr[lo], inst.row_ptr[hi]
-        rp = inst.row_ptr[lo:hi + 1] - a
+        rp, a, b = replicas.shard_rows(inst.row_ptr, lo, hi)
         f = oracle.forward(n, inst.basis[lo:hi], psi, w, rp, inst.outcome[a:b], inst.count[a:b],
                            inst.shots[lo:hi], B=M)
         g = oracle.adjoint(n, inst.basis[lo:hi], psi, w, rp, inst.outcome[a:b], f["c_obs"], B=M)
-        G = torch.from_numpy(np.ascontiguousarray(g["G_psi"]).view(np.float64).copy())
-        hL = torch.tensor(list(g["h"]) + [f["loss"]], dtype=torch.float64)
-        dist.all_reduce(G, op=dist.ReduceOp.SUM)
-        dist.all_reduce(hL, op=dist.ReduceOp.SUM)
+        # the exchange the GPU shards use (replicas.allreduce_evaluation), here over gloo in FP64
+        loss = torch.tensor([f["loss"]], dtype=torch.float64)
+        grad = torch.from_numpy(g["grad_psi"].copy())
+        gw = torch.from_numpy(g["grad_w"].copy())
+        replicas.allreduce_evaluation(loss, grad, gw, dist)
         full = oracle.forward(n, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots)
         fadj = oracle.adjoint(n, inst.basis, psi, w, inst.row_ptr, inst.outcome, full["c_obs"])
-        np.testing.assert_allclose(G.numpy().view(np.complex128).reshape(K, -1), fadj["G_psi"], atol=1e-14)
-        np.testing.assert_allclose(hL.numpy()[:K], fadj["h"], rtol=1e-12)
-        assert abs(hL[K].item() - full["loss"]) <= 1e-12 * max(1.0, abs(full["loss"]))
+        np.testing.assert_allclose(grad.numpy(), fadj["grad_psi"], atol=1e-14)
+        np.testing.assert_allclose(gw.numpy(), fadj["grad_w"], rtol=1e-12)
+        assert abs(loss.item() - full["loss"]) <= 1e-12 * max(1.0, abs(full["loss"]))
+        # the same exchange in FP32 complex64 / float32 (the GPU path's dtypes)
+        g32 = torch.from_numpy(np.ascontiguousarray(g["grad_psi"]).astype(np.complex64))
+        gw32 = torch.from_numpy(np.ascontiguousarray(g["grad_w"]).astype(np.float32))
+        replicas.allreduce_evaluation(torch.tensor([f["loss"]], dtype=torch.float64), g32, gw32, dist)
+        np.testing.assert_allclose(g32.numpy(), fadj["grad_psi"], atol=1e-6 * np.abs(fadj["grad_psi"]).max())
+        np.testing.assert_allclose(gw32.numpy(), fadj["grad_w"], rtol=1e-5)
         # aggregation: rank r reports (10 + r) ms and (r + 1) * 100 units
         ms, units = replicas.aggregate(10.0 + rank, (rank + 1) * 100.0, dist)
         assert ms == 10.0 + (world - 1) and units == 100.0 * world * (world + 1) / 2
