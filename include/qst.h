@@ -284,6 +284,9 @@ typedef struct qst_step_params {
     double mu, tau, tau_acc, eta0, eta_ratio;
     int n_eta;
     int n_krylov;  /* Krylov vectors of the spectral step (Table I: at most 30; default 30) */
+    int rank_fix;  /* spectral step: 0 = the candidate with the least Q_t (default); R > 0 = only the
+                      candidate with min(R, L_t) Ritz pairs (the known-rank variant of Sec. IV's
+                      ablation), which P_tau may still prune */
 } qst_step_params;
 void qst_step_params_default(qst_step_params *sp);
 qst_status qst_step(qst_plan plan, int slot, int r, float *psi, float *w,
@@ -316,6 +319,17 @@ typedef struct qst_iter_params {
     qst_step_params step;  /* mu, tau, tau_acc, step grid (qst_step_params_default) */
     int T_alpha;           /* coefficient slots: (t + 1) mod T_alpha == 0 (default 5) */
     int T_ref;             /* refactor slots: (t + 1) mod T_ref == 0 (default 50; 0 = never) */
+    int delta_window;      /* stopping rule (Table I, delta_20): after accepted update i, stop when
+                              (J_{i-w} - J_i) / |J_{i-w}| < delta_tol over the last w accepted updates
+                              (default 20; 0 = off; at most 63) */
+    double delta_tol;      /* default 1e-4 */
+    long long max_oracle_calls; /* stopping rule N_oracle: stop once the serial-equivalent oracle calls
+                              reach this count (default 1e5; 0 = off).  One call is one primitive of
+                              Sec. III-B over all outcomes for one atom (a response, G v) or one loss /
+                              A^T c evaluation, as Algorithm 1 issues them: the starting state costs
+                              R + 1; an atom slot 1 + 2 per trial; a coefficient slot 1 + 1 per trial;
+                              a refactor slot (new atoms) + 1.  A trial count is the accepted trial's
+                              index + 1, or the whole grid when none is accepted. */
 } qst_iter_params;
 void qst_iter_params_default(qst_iter_params *ip);
 qst_status qst_iterate(qst_plan plan, int T, int t0, float *psi, float *w,
@@ -323,6 +337,16 @@ qst_status qst_iterate(qst_plan plan, int T, int t0, float *psi, float *w,
                        const uint32_t *outcome, const uint32_t *count,
                        const uint32_t *shots, const qst_iter_params *params,
                        double *J_hist, int *accepted_hist, void *stream);
+
+/*
+ * State of the plan's device iteration after the last qst_iterate (waits for
+ * the device): whether a stopping rule has fired (iterations after it leave
+ * the state unchanged, their J_hist entries repeat J and their accepted_hist
+ * entries are 0), the serial-equivalent oracle calls and accepted updates
+ * since the run started at t0 = 0, and the current J.  Any pointer may be NULL.
+ */
+qst_status qst_iterate_state(qst_plan plan, int *stopped, long long *oracle_calls,
+                             int *accepted_updates, double *J);
 
 /*
  * Batched evaluation of many independent instances of uneven shape

@@ -375,7 +375,7 @@ def spectral_candidates(lam, eta, mu, tau, L):
 
 
 def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, eta0=1.0, eta_ratio=0.5,
-         n_eta=11, n_krylov=30):
+         n_eta=11, n_krylov=30, rank_fix=0):
     """One slot of Algorithm 1 with the step grid of Sec. IV (eta = eta0 * eta_ratio^j,
     j = 0..n_eta-1, largest first; the first accepted proposal is kept) and the
     acceptance rule J(X~) <= J_t - tau_acc (Eq. state-acceptance-rule).
@@ -387,7 +387,9 @@ def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, e
              one proposal, no step grid.
       slot 3 (T_rho): the spectral step of Sec. III-C with eta_rho from the step grid:
              Ritz pairs of S_t = rho_t + eta G_t (krylov_ritz), candidates and their
-             scores (spectral_candidates, L_t = K), the best candidate, acceptance.
+             scores (spectral_candidates, L_t = K), the best candidate, acceptance;
+             with rank_fix > 0 the candidate with min(rank_fix, L_t) Ritz pairs is taken
+             instead of the best (the known-rank variant of the ablation in Sec. IV).
     Zero-weight slots are inactive.  Returns (psi, w, J, accepted, eta)."""
     psi = np.array(psi, dtype=np.complex128)
     w = np.array(w, dtype=np.float64)
@@ -408,7 +410,10 @@ def step(n, data, psi, w, slot, r, eps=1e-8, mu=1e-3, tau=1e-3, tau_acc=1e-10, e
         K = psi.shape[0]
         for eta in etas:
             lam, Phi = krylov_ritz(n, data, psi, w, f0["c_obs"], eta, n_krylov)
-            s_star, cands = spectral_candidates(lam, eta, mu, tau, min(K, lam.size))
+            L = min(K, lam.size)
+            s_star, cands = spectral_candidates(lam, eta, mu, tau, L)
+            if rank_fix > 0:
+                s_star = min(rank_fix, L)
             keep, b, _ = cands[s_star - 1]
             pt = np.zeros_like(psi)
             wt = np.zeros_like(w)

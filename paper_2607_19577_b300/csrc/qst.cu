@@ -802,6 +802,7 @@ struct AdjArgs {
     int n, r, K;
     const float2 *phi_obs = nullptr;  // [K][nnz] from the forward (the cached adjoint reads it instead of psi)
     int64_t nnz = 0;
+    const int *skip = nullptr;        // optional device flag: when set, the launch does nothing
 };
 
 // Adjoint unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -812,6 +813,7 @@ struct AdjArgs {
 // the dense c buffer at the end of the current setting.
 template <int C, int RA>
 __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
+    if (a.skip && *a.skip) return;
     using G = Geo<C, RA>;
     constexpr SmemPlan sp = smem_plan(C, true);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -923,7 +925,9 @@ template <int R>
 __global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf, const Bin *__restrict__ bins,
                                                 const int *__restrict__ n_bins, const float *__restrict__ w,
                                                 const float2 *__restrict__ psi, float2 *__restrict__ grad,
-                                                double *__restrict__ hdot, int n, int c, int K, float invB) {
+                                                double *__restrict__ hdot, int n, int c, int K, float invB,
+                                                const int *skip) {
+    if (skip && *skip) return;
     constexpr int F = 1 << R;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)K << c;
@@ -969,7 +973,8 @@ __global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf,
 // grad_w_k = -h_k with h_k = a(psi_k)^T c = <psi_k | G psi_k> (Eqs. weight-gradient,
 // atom-response): the FP64 sum of the reduction kernel's per-thread partials.
 __global__ void __launch_bounds__(256) k_hsum(const double *__restrict__ hdot, int c, float invB,
-                                              float *__restrict__ grad_w) {
+                                              float *__restrict__ grad_w, const int *skip) {
+    if (skip && *skip) return;
     __shared__ double red[kRedMax];
     const int k = blockIdx.x;
     const double *hp = hdot + ((size_t)k << c);
@@ -1333,7 +1338,7 @@ qst_status forward_core(qst_plan p, const float *psi, const float *w, const int6
                         float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache = nullptr);
 qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st,
-                        const float2 *phi_cache = nullptr);
+                        const float2 *phi_cache = nullptr, const int *skip = nullptr);
 }  // namespace
 
 extern "C" {
@@ -1683,7 +1688,7 @@ namespace {
 // The adjoint after packing and validation.
 qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st,
-                        const float2 *phi_cache) {
+                        const float2 *phi_cache, const int *skip) {
     qst_status rc = QST_OK;
     AdjArgs a;
     a.psi = reinterpret_cast<const float2 *>(psi);
@@ -1702,12 +1707,13 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
     a.src_bin_stride = 0;
     a.phi_obs = phi_cache;
     a.nnz = p->nnz;
+    a.skip = skip;
     if (p->wide) {
         rc = adjoint_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, c_obs,
                           reinterpret_cast<float2 *>(grad_psi), st);
         if (rc || !grad_w) return rc;
         const float invBw = 1.0f / (float)p->B;
-        return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w); });
+        return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w, nullptr); });
     }
     const int units = p->nb_max << p->r;
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
@@ -1720,16 +1726,16 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
     float2 *g = reinterpret_cast<float2 *>(grad_psi);
     rc = launch(p, QST_KERNEL_REDUCE, st, [&] {
         switch (p->r) {
-            case 0: k_reduce<0><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
-            case 1: k_reduce<1><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
-            case 2: k_reduce<2><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
-            case 3: k_reduce<3><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
-            default: k_reduce<4><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB); break;
+            case 0: k_reduce<0><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB, skip); break;
+            case 1: k_reduce<1><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB, skip); break;
+            case 2: k_reduce<2><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB, skip); break;
+            case 3: k_reduce<3><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB, skip); break;
+            default: k_reduce<4><<<rgrid, 256, 0, st>>>(p->zbuf, p->bins, p->n_bins, w, reinterpret_cast<const float2 *>(psi), g, p->hdot, p->n, p->c, p->K, invB, skip); break;
         }
     });
     if (rc || !grad_w) return rc;
     return launch(p, QST_KERNEL_HSUM, st, [&] {
-        k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invB, grad_w);
+        k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invB, grad_w, skip);
     });
 }
 }  // namespace
@@ -1952,7 +1958,7 @@ qst_status spectral_candidate(qst_plan p, const float *psi, const float *w, cons
     const int L = K < m ? K : m;
     if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
         k_spectral_select<<<1, 32, 0, st>>>(p->lz_lam, p->lz_Y, m, L, eta, sp.mu, sp.tau, K, p->lz_Tc, tw, p->lz_int,
-                                            p->lz_int + 1);
+                                            p->lz_int + 1, sp.rank_fix);
     });
     if (!rc && cudaMemsetAsync(trial, 0, vb * K, st) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
@@ -1973,6 +1979,7 @@ void qst_step_params_default(qst_step_params *sp) {
     sp->eta_ratio = 0.5;
     sp->n_eta = 11;
     sp->n_krylov = 30;
+    sp->rank_fix = 0;
 }
 
 qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uint8_t *basis, const int64_t *row_ptr,
@@ -2114,6 +2121,9 @@ void qst_iter_params_default(qst_iter_params *ip) {
     qst_step_params_default(&ip->step);
     ip->T_alpha = 5;
     ip->T_ref = 50;
+    ip->delta_window = 20;
+    ip->delta_tol = 1e-4;
+    ip->max_oracle_calls = 100000;
 }
 
 }  // extern "C"
@@ -2232,7 +2242,7 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
         rc = launch(p, QST_KERNEL_STEP, s, [&] { k_iter_begin<<<1, 32, 0, s>>>(p->it_state, w, K, slot); });
         if (rc) break;
         if (slot == 0) {  // atom r_t along its projected direction (Eqs. atom-direction, atom-trial)
-            rc = adjoint_core(p, psi, p->step_m1, row_ptr, outcome, p->step_c, grad, nullptr, s);
+            rc = adjoint_core(p, psi, p->step_m1, row_ptr, outcome, p->step_c, grad, nullptr, s, nullptr, done);
             if (!rc && cudaMemcpyAsync(trial, psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
                 rc = QST_ERR_CUDA;
             if (!rc) rc = step_grid(trial, w, [&](cudaStream_t ts, double eta) {
@@ -2241,7 +2251,7 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
                 });
             });
         } else if (slot == 1) {  // coefficients (Eq. coefficient-update, then P_tau)
-            rc = adjoint_core(p, psi, w, row_ptr, outcome, p->step_c, grad, p->step_gw, s);
+            rc = adjoint_core(p, psi, w, row_ptr, outcome, p->step_c, grad, p->step_gw, s, nullptr, done);
             if (!rc) rc = step_grid(psi, p->step_tw, [&](cudaStream_t ts, double eta) {
                 return launch(p, QST_KERNEL_STEP, ts, [&] {
                     k_coeff_trial<<<1, kProjMax, 0, ts>>>(w, p->step_gw, eta, sp.tau, K, p->step_tw, done);
@@ -2263,7 +2273,8 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
                                                 p->step_c, p->nnz);
         });
         if (!rc) rc = launch(p, QST_KERNEL_STEP, s, [&] {
-            k_iter_end<<<1, 32, 0, s>>>(p->it_state, J_hist, acc_hist, i);
+            k_iter_end<<<1, 32, 0, s>>>(p->it_state, J_hist, acc_hist, i, slot, sp.n_eta, p->step_tw, K,
+                                        ip.delta_window, ip.delta_tol, ip.max_oracle_calls);
         });
     }
     return rc;
@@ -2283,7 +2294,8 @@ qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const ui
     qst_iter_params_default(&ip);
     if (params) ip = *params;
     const qst_step_params &sp = ip.step;
-    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0) || ip.T_alpha < 0 || ip.T_ref < 0)
+    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0) || ip.T_alpha < 0 || ip.T_ref < 0 ||
+        ip.delta_window < 0 || ip.delta_window >= kIterRing || !(ip.delta_tol >= 0.0) || ip.max_oracle_calls < 0)
         return QST_ERR_INVALID_ARG;
     if (p->wide || p->K > kProjMax) return QST_ERR_UNSUPPORTED;
     for (int i = 0; i < T; ++i)
@@ -2295,7 +2307,8 @@ qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const ui
                                (double)(uintptr_t)row_ptr, (double)(uintptr_t)outcome, (double)(uintptr_t)count,
                                (double)(uintptr_t)shots, (double)(uintptr_t)J_hist, (double)(uintptr_t)accepted_hist,
                                (double)T, (double)(t0 == 0 ? -1 : t0 % period), sp.mu, sp.tau, sp.tau_acc, sp.eta0,
-                               sp.eta_ratio, (double)sp.n_eta, (double)ip.T_alpha, (double)ip.T_ref};
+                               sp.eta_ratio, (double)sp.n_eta, (double)ip.T_alpha, (double)ip.T_ref,
+                               (double)ip.delta_window, ip.delta_tol, (double)ip.max_oracle_calls};
     if (!p->it_exec || key != p->it_key) {
         if (p->it_exec) {
             cudaGraphExecDestroy(p->it_exec);
@@ -2334,6 +2347,19 @@ qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const ui
     const cudaError_t le = cudaGraphLaunch(p->it_exec, st);
     if (le != cudaSuccess) return graph_fail("cudaGraphLaunch", le);
     p->total_launches += p->it_launches;
+    return QST_OK;
+}
+
+qst_status qst_iterate_state(qst_plan p, int *stopped, long long *oracle_calls, int *accepted_updates,
+                             double *J) {
+    if (!p || !p->it_state) return QST_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QST_ERR_CUDA;
+    IterState h;
+    if (cudaMemcpy(&h, p->it_state, sizeof(IterState), cudaMemcpyDeviceToHost) != cudaSuccess) return QST_ERR_CUDA;
+    if (stopped) *stopped = h.stopped;
+    if (oracle_calls) *oracle_calls = h.oracle_calls;
+    if (accepted_updates) *accepted_updates = h.n_acc;
+    if (J) *J = h.J;
     return QST_OK;
 }
 

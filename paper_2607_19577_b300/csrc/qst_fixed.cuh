@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
 // rounds: forward rounds 0, 1, 2, the c multiply in round 2's layout, inverse
 // rounds 2, 1, 0 and the accumulator z (TMEM) in round 0's layout.
 __global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx(const AdjArgs a) {
+    if (a.skip && *a.skip) return;
     constexpr FxSmem sp = fx_smem(true);
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *work = reinterpret_cast<float2 *>(smem + sp.work);

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kFxT, 4) k_forward_fx1(const FwdArgs a) {
 // publishes the scatter), the c multiply, inverse rounds 2, 1, 0, and z from
 // registers (round-0 layout).
 __global__ void __launch_bounds__(kFxT, 4) k_adjoint_fx1(const AdjArgs a) {
+    if (a.skip && *a.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *work = reinterpret_cast<float2 *>(smem);
     float *cden = reinterpret_cast<float *>(smem + 8 * kFxBuf);

@@ -158,16 +158,20 @@ __global__ void __launch_bounds__(kRefacMax) k_heig(const double2 *__restrict__ 
 // dropped).  The first minimum wins.  Writes the kept Ritz coefficients
 // Tc (m x K: column j = Y column of the j-th kept pair), the weights w_out
 // (K, zero beyond the kept count) and kout.  One thread.
+// rank_fix > 0 considers only the candidate with min(rank_fix, L) Ritz pairs
+// (the known-rank variant of the ablation of Sec. IV).
 __global__ void k_spectral_select(const double *__restrict__ lam, const double2 *__restrict__ Y, int m, int L,
                                   double eta, double mu, double tau, int K, double2 *__restrict__ Tc,
-                                  float *__restrict__ w_out, int *__restrict__ kout, int *__restrict__ s_out) {
+                                  float *__restrict__ w_out, int *__restrict__ kout, int *__restrict__ s_out,
+                                  int rank_fix) {
     if (threadIdx.x | blockIdx.x) return;
     double best = 0.0;
     int best_s = 1;
     int keep[kRefacMax], bkeep[kRefacMax];
     double b[kRefacMax], bb[kRefacMax];
     int nbest = 0;
-    for (int s = 1; s <= L; ++s) {
+    const int s_lo = rank_fix > 0 ? (rank_fix < L ? rank_fix : L) : 1;
+    for (int s = s_lo; s <= L && (rank_fix <= 0 || s == s_lo); ++s) {
         // projection of lam_1..s onto the simplex
         double css = 0.0, theta = 0.0;
         for (int j = 0; j < s; ++j) {
@@ -207,7 +211,7 @@ __global__ void k_spectral_select(const double *__restrict__ lam, const double2 
             ql += b[j] * lam[keep[j]];
         }
         const double q = (q2 - 2.0 * ql) / (2.0 * eta) + mu * (double)nk;
-        if (s == 1 || q < best) {
+        if (s == s_lo || q < best) {
             best = q;
             best_s = s;
             nbest = nk;

@@ -414,6 +414,7 @@ __device__ __forceinline__ void k2p_load_B(f2p (&X)[32], f2p (&Y)[32], const flo
 // A thread's round-A (round-B) exchange addresses are the same in both
 // directions, so it only overwrites addresses that it has read itself.
 __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
+    if (a.skip && *a.skip) return;
     constexpr K2Smem sp = k2p_smem();
     extern __shared__ __align__(16) unsigned char smem[];
     float *cbuf = reinterpret_cast<float *>(smem + sp.fbuf);
@@ -606,6 +607,7 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 }
 
 __global__ void __launch_bounds__(k2T, 2) k_adjoint_2c(const AdjArgs a) {
+    if (a.skip && *a.skip) return;
     constexpr K2cSmem sp = k2c_smem();
     extern __shared__ __align__(16) unsigned char smem[];
     uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);

@@ -45,11 +45,13 @@ class _Params(ctypes.Structure):
 class _StepParams(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("tau", ctypes.c_double), ("tau_acc", ctypes.c_double),
                 ("eta0", ctypes.c_double), ("eta_ratio", ctypes.c_double), ("n_eta", ctypes.c_int),
-                ("n_krylov", ctypes.c_int)]
+                ("n_krylov", ctypes.c_int), ("rank_fix", ctypes.c_int)]
 
 
 class _IterParams(ctypes.Structure):
-    _fields_ = [("step", _StepParams), ("T_alpha", ctypes.c_int), ("T_ref", ctypes.c_int)]
+    _fields_ = [("step", _StepParams), ("T_alpha", ctypes.c_int), ("T_ref", ctypes.c_int),
+                ("delta_window", ctypes.c_int), ("delta_tol", ctypes.c_double),
+                ("max_oracle_calls", ctypes.c_longlong)]
 
 
 _lib = None
@@ -75,6 +77,8 @@ def load():
         lib.qst_iter_params_default.argtypes = [ctypes.POINTER(_IterParams)]
         lib.qst_iter_params_default.restype = None
         lib.qst_iterate.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_IterParams), P, P, P]
+        lib.qst_iterate_state.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(i32), ctypes.POINTER(f64)]
         lib.qst_forward.argtypes = [P] + [P] * 11 + [P]
         lib.qst_adjoint.argtypes = [P] + [P] * 8 + [P]
         lib.qst_evaluate_host.argtypes = [P] + [P] * 11 + [P]
@@ -95,7 +99,7 @@ def load():
         lib.qst_step_params_default.restype = None
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
                                  ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(f64), P]
-        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_tangent", "qst_iterate", "qst_forward",
+        for name in ["qst_plan_create", "qst_plan_destroy", "qst_plan_workspace_bytes", "qst_plan_geometry", "qst_tangent", "qst_iterate", "qst_iterate_state", "qst_forward",
                      "qst_adjoint", "qst_evaluate", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
@@ -323,17 +327,21 @@ class Plan:
                                ctypes.byref(acc), ctypes.byref(eta), _stream()), "qst_step")
         return J.value, bool(acc.value), eta.value
 
-    def iterate(self, T, t0, psi, w, d: Data, J_hist=None, accepted=None, T_alpha=5, T_ref=50, **step_params):
+    def iterate(self, T, t0, psi, w, d: Data, J_hist=None, accepted=None, T_alpha=5, T_ref=50, delta_window=20,
+                delta_tol=1e-4, max_oracle_calls=100000, **step_params):
         """qst_iterate: T iterations of Algorithm 1 from iteration t0, in place on psi
         and w, every decision on the device (one CUDA graph, replayed on later calls
-        with the same buffers).  Returns device tensors (J_hist float64 [T],
-        accepted int32 [T]); nothing is synchronised."""
+        with the same buffers), with the stopping rules of Table I (delta over the
+        last delta_window accepted updates below delta_tol, or max_oracle_calls
+        serial-equivalent oracle calls; 0 disables either).  Returns device tensors
+        (J_hist float64 [T], accepted int32 [T]); nothing is synchronised."""
         _need(psi, torch.complex64, (self.K, self.D), "psi")
         _need(w, torch.float32, (self.K,), "w")
         self._data(d)
         ip = _IterParams()
         load().qst_iter_params_default(ctypes.byref(ip))
         ip.T_alpha, ip.T_ref = int(T_alpha), int(T_ref)
+        ip.delta_window, ip.delta_tol, ip.max_oracle_calls = int(delta_window), float(delta_tol), int(max_oracle_calls)
         for k, v in step_params.items():
             setattr(ip.step, k, v)
         J_hist = torch.empty(T, dtype=torch.float64, device="cuda") if J_hist is None else J_hist
@@ -342,6 +350,13 @@ class Plan:
                                   _ptr(d.outcome), _ptr(d.count), _ptr(d.shots), ctypes.byref(ip), _ptr(J_hist),
                                   _ptr(accepted), _stream()), "qst_iterate")
         return J_hist, accepted
+
+    def iterate_state(self):
+        """qst_iterate_state (synchronises): dict(stopped, oracle_calls, accepted_updates, J)."""
+        st, calls, acc, J = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int(), ctypes.c_double()
+        _check(load().qst_iterate_state(self._h, ctypes.byref(st), ctypes.byref(calls), ctypes.byref(acc),
+                                        ctypes.byref(J)), "qst_iterate_state")
+        return {"stopped": bool(st.value), "oracle_calls": calls.value, "accepted_updates": acc.value, "J": J.value}
 
     def status(self):
         """Synchronise and return the device status bits (0 = clean)."""

@@ -163,15 +163,16 @@ def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref, round
     # device-driven: first T iterations, a replay of the same graph from the
     # same start, then the next T iterations (t0 = T continues the atom cycle)
     dp, dw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
-    J1, a1 = plan.iterate(T, 0, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref)
+    off = dict(delta_window=0, max_oracle_calls=0)  # this test compares schedules, not stopping rules
+    J1, a1 = plan.iterate(T, 0, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref, **off)
     first = (J1.cpu().numpy().copy(), a1.cpu().numpy().copy(), dp.clone(), dw.clone())
     dp.copy_(torch.from_numpy(psi0))
     dw.copy_(torch.from_numpy(w0))
-    J1, a1 = plan.iterate(T, 0, dp, dw, d, J_hist=J1, accepted=a1, T_alpha=T_alpha, T_ref=T_ref)
+    J1, a1 = plan.iterate(T, 0, dp, dw, d, J_hist=J1, accepted=a1, T_alpha=T_alpha, T_ref=T_ref, **off)
     torch.cuda.synchronize()
     assert np.array_equal(J1.cpu().numpy(), first[0]) and np.array_equal(a1.cpu().numpy(), first[1])
     assert torch.equal(dp, first[2]) and torch.equal(dw, first[3])
-    J2, a2 = plan.iterate(T, T, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref)
+    J2, a2 = plan.iterate(T, T, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref, **off)
     torch.cuda.synchronize()
     plan.check()
     Jd = list(first[0]) + list(J2.cpu().numpy())
@@ -183,12 +184,15 @@ def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref, round
     plan.close()
 
 
-@pytest.mark.parametrize("name,K,seed", [("n4_all81", 4, 3), ("n8_m40_k4", 4, 5), ("n10_m60_k8", 8, 7)])
-def test_spectral_step_matches_oracle(name, K, seed):
+@pytest.mark.parametrize("name,K,seed,rank_fix", [("n4_all81", 4, 3, 0), ("n8_m40_k4", 4, 5, 0),
+                                                  ("n10_m60_k8", 8, 7, 0), ("n8_m40_k4", 4, 5, 2),
+                                                  ("n10_m60_k8", 8, 7, 3)])
+def test_spectral_step_matches_oracle(name, K, seed, rank_fix):
     """qst_step slot 3 (Sec. III-C: block Krylov Ritz pairs of S = rho + eta G, the
     scored candidates, the best one, acceptance over the step grid) against the
     oracle's slot 3: same acceptance and step, J within 1e-5, and the same state at
-    the rho level.  At n = 4 the Krylov space spans C^16 (exact eigenpairs)."""
+    the rho level.  At n = 4 the Krylov space spans C^16 (exact eigenpairs).  rank_fix
+    > 0 is the known-rank variant (only the candidate with that many Ritz pairs)."""
     inst = synth.make_instance(name, seed=seed, K=K)
     n = inst.n
     psi0 = inst.psi.astype(np.complex128)
@@ -199,10 +203,11 @@ def test_spectral_step_matches_oracle(name, K, seed):
     d = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
     tp = torch.from_numpy(psi0.astype(np.complex64)).cuda()
     tw = torch.from_numpy(w0.astype(np.float32)).cuda()
-    J, acc, eta = plan.step(3, 0, tp, tw, d)
+    J, acc, eta = plan.step(3, 0, tp, tw, d, rank_fix=rank_fix)
     # the oracle starts from the same (FP32-rounded) state
     op, ow, oJ, oacc, oeta = oracle.step(n, data, psi0.astype(np.complex64).astype(np.complex128),
-                                         w0.astype(np.float32).astype(np.float64), 3, 0, n_krylov=30)
+                                         w0.astype(np.float32).astype(np.float64), 3, 0, n_krylov=30,
+                                         rank_fix=rank_fix)
     assert acc == oacc and abs(eta - oeta) <= 1e-12 * max(1.0, oeta), (acc, oacc, eta, oeta)
     assert abs(J - oJ) <= 1e-5 * abs(oJ), (J, oJ)
     gp = tp.cpu().numpy().astype(np.complex128)
@@ -211,5 +216,74 @@ def test_spectral_step_matches_oracle(name, K, seed):
     assert a.sum() == b.sum()
     np.testing.assert_allclose(np.sort(gw[a]), np.sort(ow[b]), atol=2e-5)
     assert _gram_frob2(gp[a], gw[a], op[b], ow[b]) <= 1e-8
-    np.testing.assert_allclose(gp[a].conj() @ gp[a].T, np.eye(a.sum()), atol=2e-5)
+    if acc:  # an accepted spectral step leaves orthonormal Ritz vectors (a rejected one the old atoms)
+        np.testing.assert_allclose(gp[a].conj() @ gp[a].T, np.eye(a.sum()), atol=2e-5)
+        if rank_fix:
+            assert a.sum() <= rank_fix
+    plan.close()
+
+
+def _host_calls(slot, acc, eta, R_new, n_eta=11, eta0=1.0, ratio=0.5):
+    """Serial-equivalent oracle calls of one Algorithm 1 slot (the reading the device
+    counter uses): atom slot 1 + 2 per trial, coefficient slot 1 + 1 per trial,
+    refactor slot (new atoms) + 1; trials = accepted index + 1, else the grid."""
+    trials = int(round(np.log(eta / eta0) / np.log(ratio))) + 1 if acc else n_eta
+    if slot == 0:
+        return 1 + 2 * trials
+    if slot == 1:
+        return 1 + trials
+    return R_new + 1
+
+
+@pytest.mark.parametrize("window,tol,max_calls", [(4, 2e-3, 0), (0, 0.0, 60), (6, 5e-3, 100000)])
+def test_device_stopping_rules_match_the_host_rule(window, tol, max_calls):
+    """Table I's stopping rules inside qst_iterate (no host synchronisation): the
+    relative decrease of J over the last `window` accepted updates below `tol`,
+    or `max_calls` serial-equivalent oracle calls.  The same schedule driven from
+    the host with qst_step, with the rule evaluated on the host, stops at the same
+    iteration with the same J history (bitwise), oracle-call count and accepted
+    updates; after the stop the device leaves the state unchanged."""
+    inst = synth.make_instance("n8_m40_k4", seed=21, K=4)
+    psi0 = inst.psi.astype(np.complex128)
+    psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
+    psi0 = psi0.astype(np.complex64)
+    w0 = inst.w.astype(np.float32)
+    plan = qst.Plan(inst.n, inst.M, 4, inst.nnz)
+    d = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    T, T_alpha = 40, 5
+    hp, hw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
+    R0 = int(np.count_nonzero(w0 > 0))
+    calls = R0 + 1
+    _, _, loss0 = plan.forward(hp, hw, d)
+    Jrec = [loss0.item() + 1e-3 * R0]  # J after accepted update i (i = 0: the start; mu = 1e-3)
+    Jh, acc_h, count, stop_at = [], [], 0, None
+    for t in range(T):
+        slot = _schedule(t, T_alpha, 0)
+        r = 0
+        if slot == 0:
+            act = [k for k, v in enumerate(hw.cpu().numpy()) if v > 0]
+            r = act[count % len(act)]
+            count += 1
+        J, acc, eta = plan.step(slot, r, hp, hw, d)
+        Jh.append(J)
+        acc_h.append(acc)
+        calls += _host_calls(slot, acc, eta, int(np.count_nonzero(hw.cpu().numpy() > 0)))
+        if acc:
+            Jrec.append(J)
+        n_acc = len(Jrec) - 1
+        fired = window > 0 and acc and n_acc >= window and (Jrec[n_acc - window] - J) / abs(Jrec[n_acc - window]) < tol
+        if fired or (max_calls > 0 and calls >= max_calls):
+            stop_at = t
+            break
+    assert stop_at is not None, "the rule must fire within the run"
+    dp, dw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
+    Jd, ad = plan.iterate(T, 0, dp, dw, d, T_alpha=T_alpha, T_ref=0, delta_window=window, delta_tol=tol,
+                          max_oracle_calls=max_calls)
+    st = plan.iterate_state()
+    Jd, ad = Jd.cpu().numpy(), ad.cpu().numpy()
+    assert st["stopped"]
+    assert list(Jd[:stop_at + 1]) == Jh and [bool(x) for x in ad[:stop_at + 1]] == acc_h
+    assert np.all(Jd[stop_at + 1:] == Jh[-1]) and not ad[stop_at + 1:].any()
+    assert st["oracle_calls"] == calls and st["accepted_updates"] == sum(acc_h)
+    assert torch.equal(dp, hp) and torch.equal(dw, hw)
     plan.close()

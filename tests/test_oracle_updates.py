@@ -296,8 +296,9 @@ def _prune_dense(beta):
     return keep, b / b.sum()
 
 
-def _dense_step(inst, psi, w, slot, r):
-    """(psi~, w~, J, accepted, eta) of one Algorithm 1 slot, dense route."""
+def _dense_step(inst, psi, w, slot, r, rank_fix=0):
+    """(psi~, w~, J, accepted, eta) of one Algorithm 1 slot, dense route (rank_fix:
+    the spectral slot takes the candidate with that many eigenpairs)."""
     psi = np.array(psi, complex)
     w = np.array(w, float)
     K, D = psi.shape
@@ -333,7 +334,8 @@ def _dense_step(inst, psi, w, slot, r):
             lam, V = np.linalg.eigh(rho + eta * G)
             lam, V = lam[::-1], V[:, ::-1]
             best = None
-            for s_ in range(1, min(K, D) + 1):
+            L = min(K, D)
+            for s_ in (range(1, L + 1) if rank_fix <= 0 else [min(rank_fix, L)]):
                 keep, b = _prune_dense(_proj_bisect(lam[:s_]))
                 q = (np.dot(b, b) - 2.0 * np.dot(b, lam[keep])) / (2.0 * eta) + STEP_MU * len(keep)
                 if best is None or q < best[0]:
@@ -424,3 +426,17 @@ def test_oracle_tangent_against_dense_projector_and_fd(n, K, seed):
         fd = (vals[0] - vals[1]) / (2 * t)
         want = -2.0 * np.sum(np.abs(d[k]) ** 2)
         assert abs(fd - want) <= 1e-6 * abs(want) + 1e-12, (k, fd, want)
+
+
+@pytest.mark.parametrize("rank_fix", [1, 2, 3])
+def test_oracle_spectral_slot_with_a_fixed_rank_equals_dense_route(rank_fix):
+    """The known-rank variant of the spectral slot (Sec. IV ablation: the candidate with
+    R Ritz pairs) against the dense route: same acceptance, step, J and rho."""
+    inst, psi, w = _step_case(3, 4, 1000)
+    po, wo, Jo, acc_o, eta_o = oracle.step(4, _data(inst), psi, w, 3, 0, rank_fix=rank_fix)
+    pd, wd, Jd, acc_d, eta_d = _dense_step(inst, psi, w, 3, 0, rank_fix=rank_fix)
+    assert acc_o == acc_d and eta_o == eta_d
+    assert abs(Jo - Jd) <= 1e-10 * max(1.0, abs(Jd))
+    np.testing.assert_allclose(_rho_of(po, wo), _rho_of(pd, wd), atol=1e-10)
+    if acc_o:
+        assert np.count_nonzero(wo > 0) <= rank_fix
