@@ -390,7 +390,8 @@ def run_ours(args):
     # roofline of the dominant kernel
     fwd_ops, adj_ops, inv_ops = algorithmic_ops(inst.basis, K, D)
     geo = plan.geometry()
-    cached = geo["fixed_rounds"] == 2 and args.phi_cache != 0
+    wide = n > 16
+    cached = (geo["fixed_rounds"] == 2 and args.phi_cache != 0) or (wide and args.phi_cache == 1)
     # per-step kernel time (the wide path launches its chunk kernels once per setting group)
     la, ms_adj = stats["adjoint"]
     lf, ms_fwd = stats["forward"]
@@ -405,8 +406,11 @@ def run_ours(args):
     peak_alu = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # TFLOP/s, 1 per lane-op
     adj_work = inv_ops if cached else adj_ops  # the adjoint kernel's own algorithmic work
     achieved = adj_work / (adj_ms / 1e3) / 1e12
-    adj_kernel = ("k_adjoint_2c" if cached else
-                  {2: "k_adjoint_2r", 1: "k_adjoint_fx"}.get(geo["fixed_rounds"], "k_adjoint"))
+    if wide:
+        adj_kernel = ("k_adjoint_fx1c" if cached else "k_adjoint_fx1") if geo["fixed_rounds"] == 1 else "k_adjoint"
+    else:
+        adj_kernel = ("k_adjoint_2c" if cached else
+                      {2: "k_adjoint_2r", 1: "k_adjoint_fx"}.get(geo["fixed_rounds"], "k_adjoint"))
     traffic = None
     prof = os.path.join(ROOT, "profiles", "adjoint_traffic.json")
     if os.path.exists(prof):
@@ -428,7 +432,8 @@ def run_ours(args):
                                    "amplitude (the adjoint reads the forward's stored transforms)" if cached else
                                    "recomputed rotation + inverse rotation: 4 m_s + 8 FP32 lane-ops per amplitude"),
                 "launches_per_step": la / args.steps,
-                "forward": {"kernel": "k_forward_2r" if geo["fixed_rounds"] == 2 else "forward",
+                "forward": {"kernel": ("k_forward_fx1" if wide and geo["fixed_rounds"] == 1 else
+                                       {2: "k_forward_2r", 1: "k_forward_fx"}.get(geo["fixed_rounds"], "k_forward")),
                             "ops_per_launch": fwd_ops, "ms_per_launch": ms_fwd / args.steps,
                             "achieved": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12,
                             "frac": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12 / peak_alu},
@@ -443,7 +448,7 @@ def run_ours(args):
     # the same evaluation through qst_forward + qst_adjoint, whose adjoint
     # recomputes the rotations (the plain path's structure), for its roofline
     recompute = None
-    if cached and not args.shard:
+    if cached and not args.shard and not wide:
         def sep():
             plan.forward(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss)
             plan.adjoint(psi, w, data, c_obs, grad_psi=grad, grad_w=grad_w)

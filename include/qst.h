@@ -68,12 +68,15 @@ typedef struct qst_params {
                              exchange); 0 = rounds chosen per setting; -1 = automatic: 2 when a
                              work bin may hold >= 32 settings, else 1.  Other values:
                              QST_ERR_INVALID_ARG.  Default -1. */
-    int phi_cache;        /* qst_evaluate's transform cache (two-round plans only): the forward stores
-                             the chunk transform of every atom at every observed outcome (K x nnz
-                             complex64, owned by the plan) and the adjoint then runs its inverse
-                             rounds only.  1 = on (QST_ERR_UNSUPPORTED for other plans), 0 = off,
-                             -1 = automatic: on for two-round plans when K x nnz x 8 bytes <= 16 GiB.
-                             qst_forward and qst_adjoint never use it.  Default -1. */
+    int phi_cache;        /* qst_evaluate's transform cache: the forward stores the transform of every
+                             atom at every observed outcome (K x nnz complex64, owned by the plan) and
+                             the adjoint then runs its inverse rounds only (on the n = 20 path it also
+                             skips the high-bit pass before them).  Two-round plans and the n = 20
+                             path (12-qubit chunks).  1 = on (QST_ERR_UNSUPPORTED for other plans),
+                             0 = off, -1 = automatic: on for two-round plans when K x nnz x 8 bytes
+                             <= 16 GiB, off on the n = 20 path (whose adjoint recomputes the rotated
+                             amplitudes unless asked).  qst_forward and qst_adjoint never use it.
+                             Default -1. */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;
@@ -352,7 +355,8 @@ qst_status qst_iterate_state(qst_plan plan, int *stopped, long long *oracle_call
  * Batched evaluation of many independent instances of uneven shape
  * (instances with different n, M, K and shots, e.g. 64 instances with n from
  * 6 to 14).  qst_batch_create makes one plan per instance (params shared).
- * qst_batch_evaluate runs every instance's qst_forward + qst_adjoint; arguments
+ * qst_batch_evaluate runs every instance's qst_evaluate (qst_forward + qst_adjoint,
+ * with the instance plan's transform cache where it has one); arguments
  * are HOST arrays of `count` DEVICE pointers, one per instance, with the
  * per-instance layouts of qst_forward / qst_adjoint (loss[i] -> double[1],
  * c_obs[i] -> float[nnz_i], grad_psi[i] -> complex64[K_i][2^n_i],

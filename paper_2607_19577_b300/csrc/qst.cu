@@ -1189,7 +1189,8 @@ void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t 
     }
     const int grid = units * p->K;
     if (p->fx && p->wide) {  // single-setting units
-        k_forward_fx1<<<grid, kFxT, kFx1Smem, st>>>(a);
+        if (a.phi_obs) k_forward_fx1<true><<<grid, kFxT, kFx1Smem, st>>>(a);
+        else k_forward_fx1<false><<<grid, kFxT, kFx1Smem, st>>>(a);
         return;
     }
     if (p->fx) {
@@ -1212,7 +1213,8 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a, int units, cudaStream_t 
     }
     const int grid = units * p->K;
     if (p->fx && p->wide) {  // single-setting units
-        k_adjoint_fx1<<<grid, kFxT, kFx1Smem, st>>>(a);
+        if (a.phi_obs) k_adjoint_fx1c<<<grid, kFxT, kFx1Smem, st>>>(a);
+        else k_adjoint_fx1<<<grid, kFxT, kFx1Smem, st>>>(a);
         return;
     }
     if (p->fx) {
@@ -1248,7 +1250,7 @@ namespace {
 // Wide path, forward: per atom and group of settings, the high pass into the
 // intermediate, then the chunk kernel on single-setting bins reading it.
 qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int64_t *row_ptr,
-                        const uint32_t *outcome, float *p_dense, cudaStream_t st) {
+                        const uint32_t *outcome, float *p_dense, cudaStream_t st, float2 *phi_cache) {
     const size_t D = (size_t)1 << p->n;
     const int tiles = (1 << p->c) / kWideCols;
     for (int g0 = 0; g0 < p->M; g0 += p->wide_G) {
@@ -1276,6 +1278,7 @@ qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.n = p->n;
         a.r = p->r;
         a.K = p->K;
+        a.phi_obs = phi_cache;
         const int units = G << p->r;
         rc = launch(p, QST_KERNEL_FORWARD, st, [&] {
             launch_forward_units(p, a, units, st);
@@ -1289,15 +1292,18 @@ qst_status forward_wide(qst_plan p, const float2 *psi, const float *w, const int
 // in place over the intermediate, inverse high pass accumulating into the FP64
 // accumulator; then grad = -(w/B) acc and the h partials.
 qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int64_t *row_ptr,
-                        const uint32_t *outcome, const float *c_obs, float2 *grad, cudaStream_t st) {
+                        const uint32_t *outcome, const float *c_obs, float2 *grad, cudaStream_t st,
+                        const float2 *phi_cache) {
     const size_t D = (size_t)1 << p->n;
     const int tiles = (1 << p->c) / kWideCols;
     if (cudaMemsetAsync(p->wide_acc, 0, sizeof(double2) * (size_t)p->K * D, st) != cudaSuccess) return QST_ERR_CUDA;
     for (int g0 = 0; g0 < p->M; g0 += p->wide_G) {
         const int G = (p->M - g0) < p->wide_G ? (p->M - g0) : p->wide_G;
-        qst_status rc = launch(p, QST_KERNEL_HIGH, st, [&] {
-            k_high_fwd<<<dim3(tiles, p->K), kWideT, kWideSmem, st>>>(psi, p->plans, g0, G, p->K, p->c, p->wide_T);
-        });
+        qst_status rc = QST_OK;
+        if (!phi_cache)  // with the transform cache the chunk adjoint needs no source
+            rc = launch(p, QST_KERNEL_HIGH, st, [&] {
+                k_high_fwd<<<dim3(tiles, p->K), kWideT, kWideSmem, st>>>(psi, p->plans, g0, G, p->K, p->c, p->wide_T);
+            });
         if (!rc) rc = launch(p, QST_KERNEL_HIGH, st, [&] { k_wide_bins<<<1, 256, 0, st>>>(g0, G, p->bins, p->n_bins); });
         if (rc) return rc;
         AdjArgs a;
@@ -1315,6 +1321,8 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
         a.n = p->n;
         a.r = p->r;
         a.K = p->K;
+        a.phi_obs = phi_cache;
+        a.nnz = p->nnz;
         const int units = G << p->r;
         rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
             launch_adjoint_units(p, a, units, st);
@@ -1429,7 +1437,9 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (p->smax >= 32 ? 2 : 1);
     p->fx2 = c == 12 && fr == 2 && !wide;
     p->fx = c == 12 && p->A == 4 && (fr == 1 || (fr == 2 && wide));
-    if (prm.phi_cache == 1 && !p->fx2) {  // the cached adjoint exists for the two-round kernels only
+    // the cached adjoint exists for the two-round kernels and the wide path's single-setting
+    // 12-qubit-chunk kernels (n = 20)
+    if (prm.phi_cache == 1 && !p->fx2 && !(wide && p->fx)) {
         delete p;
         return QST_ERR_UNSUPPORTED;
     }
@@ -1484,8 +1494,11 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     // qst_evaluate's transform cache: K x nnz complex values (1 GB for the
     // n = 16, M = 4096, K = 16 workload); automatic for two-round plans up to 16 GiB
-    if (!rc && p->fx2 && nnz > 0 &&
-        (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30))))
+    // (on the wide path with 12-qubit chunks, n = 20, only when asked for: there the adjoint
+    // recomputes by default)
+    if (!rc && nnz > 0 &&
+        ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30)))) ||
+         (wide && p->fx && prm.phi_cache == 1)))
         rc = dalloc(p, &p->phi, (size_t)K * nnz);
     if (!rc) rc = dalloc(p, &p->it_state, 1);
     if (!rc && cudaMemset(p->it_state, 0, sizeof(IterState)) != cudaSuccess) rc = QST_ERR_CUDA;
@@ -1504,8 +1517,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_adjoint_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
         }
         if (p->wide) {
-            cudaFuncSetAttribute(k_forward_fx1, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
+            cudaFuncSetAttribute(k_forward_fx1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
+            cudaFuncSetAttribute(k_forward_fx1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
             cudaFuncSetAttribute(k_adjoint_fx1, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
+            cudaFuncSetAttribute(k_adjoint_fx1c, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
             cudaFuncSetAttribute(k_high_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideSmem);
             cudaFuncSetAttribute(k_high_inv_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideInvSmem);
         }
@@ -1624,7 +1639,7 @@ qst_status forward_core(qst_plan p, const float *psi, const float *w, const int6
     if (p_dense && cudaMemsetAsync(p_dense, 0, (size_t)p->M * ((size_t)1 << p->n) * sizeof(float), st) != cudaSuccess)
         return QST_ERR_CUDA;
     if (p->wide) {
-        rc = forward_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, p_dense, st);
+        rc = forward_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, p_dense, st, phi_cache);
         if (rc) return rc;
     }
     FwdArgs a;
@@ -1710,7 +1725,7 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
     a.skip = skip;
     if (p->wide) {
         rc = adjoint_wide(p, reinterpret_cast<const float2 *>(psi), w, row_ptr, outcome, c_obs,
-                          reinterpret_cast<float2 *>(grad_psi), st);
+                          reinterpret_cast<float2 *>(grad_psi), st, phi_cache);
         if (rc || !grad_w) return rc;
         const float invBw = 1.0f / (float)p->B;
         return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w, nullptr); });
@@ -2613,11 +2628,10 @@ extern "C" qst_status qst_batch_evaluate(qst_batch b, const float *const *psi, c
             if (cudaStreamWaitEvent(b->streams[j], b->start, 0) != cudaSuccess) rc = QST_ERR_CUDA;
         for (int i = 0; i < b->count && !rc; ++i) {
             void *si = (void *)b->streams[i % ns];
-            rc = qst_forward(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i], nullptr,
-                             c_obs[i], loss[i], nullptr, si);
-            if (!rc)
-                rc = qst_adjoint(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], c_obs[i], grad_psi[i],
-                                 grad_w[i], si);
+            // qst_evaluate: with the instance plan's transform cache (two-round plans) the
+            // adjoint applies only the inverse rounds
+            rc = qst_evaluate(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i], nullptr,
+                              c_obs[i], loss[i], grad_psi[i], grad_w[i], si);
         }
         for (int j = 0; j < ns && !rc; ++j)
             if (cudaEventRecord(b->join[j], b->streams[j]) != cudaSuccess || cudaStreamWaitEvent(cs, b->join[j], 0) != cudaSuccess)

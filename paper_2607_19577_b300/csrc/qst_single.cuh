@@ -36,7 +36,11 @@ __device__ __forceinline__ Fx1Unit fx1_unit(const Bin &b, uint32_t f, int nf, co
     return u;
 }
 
-// Forward unit = (single-setting bin, high pattern f, atom k).
+// Forward unit = (single-setting bin, high pattern f, atom k).  CACHE (the
+// evaluate path with the transform cache): the round-2 values also go to the
+// exchange buffer and the gather stores them, unscaled, at the observed
+// outcomes into the atom's slice of a.phi_obs.
+template <bool CACHE>
 __global__ void __launch_bounds__(kFxT, 4) k_forward_fx1(const FwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *work = reinterpret_cast<float2 *>(smem);
@@ -67,11 +71,16 @@ __global__ void __launch_bounds__(kFxT, 4) k_forward_fx1(const FwdArgs a) {
     const float sc = a.w[k] * us.cs;
 #pragma unroll
     for (int i = 0; i < 16; ++i) pbuf[b2 + fx_roff<2>(i)] = sc * (v[i].x * v[i].x + v[i].y * v[i].y);
+    if (CACHE) {
+        __syncwarp();  // the warp's round-2 reads of the exchange buffer are done (fx_exchange's last load)
+        fx_store<2>(v, work, b2);
+    }
     __syncthreads();
     float *pk = a.ppart + (size_t)k * a.nnz;
     for (int j = tid; j < us.cnt; j += kFxT) {
         const uint32_t u = a.outcome[us.lo + j] & cmask;
         pk[us.lo + j] = pbuf[fx_pidx(u)];
+        if (CACHE) a.phi_obs[(size_t)k * a.nnz + us.lo + j] = work[fx_pidx(u)];
     }
     if (a.p_dense) {
         const int s = a.order[b.start];
@@ -122,6 +131,49 @@ __global__ void __launch_bounds__(kFxT, 4) k_adjoint_fx1(const AdjArgs a) {
         v[i].x *= cc;
         v[i].y *= cc;
     }
+#pragma unroll
+    for (int R = 2; R >= 0; --R) {
+        butterfly_inv<4>(v, fx_bits(us.xy, R), fx_bits(us.y, R));
+        if (R > 0) fx_exchange(v, work, R, R - 1, b0, b1, b2);
+    }
+    float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << 12);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) zo[tid + (i << 8)] = v[i];
+}
+
+// Cached adjoint unit (the evaluate path with the transform cache): the
+// forward stored the setting's chunk transform phi at its observed outcomes,
+// so y = c 2^-m phi is scattered into the zeroed exchange buffer, loaded in
+// round 2's layout, and only the inverse rounds 2, 1, 0 run; z from registers
+// (round-0 layout) over the group's intermediate, as k_adjoint_fx1 writes it.
+// No source is built and the group's high pass before the adjoint is skipped.
+__global__ void __launch_bounds__(kFxT, 4) k_adjoint_fx1c(const AdjArgs a) {
+    if (a.skip && *a.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *work = reinterpret_cast<float2 *>(smem);
+    const uint32_t tid = threadIdx.x;
+    const int unit = blockIdx.x;
+    const int k = unit % a.K;
+    const int rest = unit / a.K;
+    const uint32_t f = rest & ((1u << a.r) - 1u);
+    const int bin = rest >> a.r;
+    if (bin >= *a.n_bins) return;
+    const Bin b = a.bins[bin];
+    const int D = 1 << a.n;
+    constexpr uint32_t cmask = 4095u;
+    const Fx1Unit us = fx1_unit(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff);
+    for (int u = tid; u < kFxBuf; u += kFxT) work[u] = make_float2(0.f, 0.f);
+    __syncthreads();  // zeroed before any entry is scattered
+    const float2 *phk = a.phi_obs + (size_t)k * a.nnz;
+    for (int j = tid; j < us.cnt; j += kFxT) {
+        const float cy = a.c_obs[us.lo + j] * us.cs;
+        const float2 ph = phk[us.lo + j];
+        work[fx_pidx(a.outcome[us.lo + j] & cmask)] = make_float2(cy * ph.x, cy * ph.y);
+    }
+    __syncthreads();  // the scatter is visible
+    const uint32_t b0 = fx_pidx(fx_ubase<0>(tid)), b1 = fx_pidx(fx_ubase<1>(tid)), b2 = fx_pidx(fx_ubase<2>(tid));
+    float2 v[16];
+    fx_load<2>(v, work, b2);
 #pragma unroll
     for (int R = 2; R >= 0; --R) {
         butterfly_inv<4>(v, fx_bits(us.xy, R), fx_bits(us.y, R));

@@ -91,3 +91,21 @@ def test_n20_identities(c5):
     c = c5["c_obs"].cpu().numpy().astype(np.float64)
     p = c5["p_obs"].cpu().numpy().astype(np.float64)
     np.testing.assert_allclose(np.dot(w, h), np.sum(c * p / inst.M), rtol=1e-5)
+
+
+@pytest.mark.parametrize("n,M,K,shots,seed", [(20, 3, 2, 10000, 12), (20, 7, 3, 3000, 13)])
+def test_wide_evaluate_with_transform_cache(n, M, K, shots, seed):
+    """The n = 20 path with the transform cache (phi_cache = 1): qst_evaluate's
+    adjoint skips the group's high pass and the forward rounds; against the oracle,
+    and bitwise equal to qst_forward + qst_adjoint (which recompute).  n = 17..19
+    (chunks below 12 qubits) refuse the cache."""
+    from test_gpu_parity import run_gpu_evaluate
+    inst = synth.random_instance(n, M, K, shots, 600 + seed)
+    ev = run_gpu_evaluate(inst, phi_cache=1)
+    compare(inst, ev, run_oracle(inst))
+    sep = run_gpu(inst, phi_cache=1)
+    for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
+        assert np.array_equal(ev[key], sep[key]), key
+    assert ev["loss"] == sep["loss"]
+    with pytest.raises(qst.QSTError):
+        qst.Plan(17, 4, 2, 10, phi_cache=1)
