@@ -62,6 +62,10 @@ def parse_args():
     ap.add_argument("--phi-cache", type=int, default=-1, choices=[-1, 0, 1],
                     help="qst_evaluate's transform cache: 1 on, 0 off (the adjoint recomputes the rotations), "
                          "-1 the plan's automatic choice")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="chunk transforms of two-round plans: 0 FP32 butterflies; 1..3 tensor-core products "
+                         "over 6-qubit groups with the data split into that many BF16 terms (the line then also "
+                         "times the FP32 plan on the same data: field vs_fp32)")
     ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="12-qubit chunk kernels: 2 = two 6-qubit rounds, 1 = three 4-qubit rounds, "
                          "0 = rounds chosen per setting, -1 = the plan's automatic choice")
@@ -300,6 +304,81 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def tc_mma_flops(inst, r, T):
+    """FLOPs the tensor-core chunk kernels issue per launch (forward or adjoint):
+    per setting, high pattern and atom pair, 2 products x T data terms x 8
+    K-steps of one M = N = 128, K = 16 MMA (2 M N K FLOPs each)."""
+    return float(inst.M) * (1 << r) * ((inst.K + 1) // 2) * 2 * T * 8 * (2 * 128 * 128 * 16)
+
+
+def tc_roofline(args, inst, geo, stats, ms_step, plain_ops, peaks, peak_alu):
+    """Roofline of the tensor-core variant: its dominant kernel's issued MMA
+    FLOPs against the measured BF16 tensor peak (cuBLAS burst)."""
+    T = args.precision
+    flops = tc_mma_flops(inst, geo["high_qubits"], T)
+    peak = float(peaks.get("bf16_tflops", 1800.0))
+    src = "MEASURED_PEAKS.json bf16_tflops (cuBLAS BF16 GEMM, burst)" if "bf16_tflops" in peaks else \
+        "fallback 1.8 PFLOP/s BF16"
+    lf, ms_fwd = stats["forward"]
+    la, ms_adj = stats["adjoint"]
+    f_ms, a_ms = ms_fwd / args.steps, ms_adj / args.steps
+    dom_adj = a_ms >= f_ms
+    ms_dom = a_ms if dom_adj else f_ms
+    part = lambda ms: {"ops_per_launch": flops, "ms_per_launch": ms,  # noqa: E731
+                       "achieved": flops / (ms / 1e3) / 1e12, "frac": flops / (ms / 1e3) / 1e12 / peak}
+    return {"bound": "tensor", "achieved": flops / (ms_dom / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / (ms_dom / 1e3) / 1e12 / peak, "traffic": None,
+            "kernel": "k_adjoint_tc" if dom_adj else "k_forward_tc", "peak_source": src,
+            "ops_per_launch": flops, "ms_per_launch": ms_dom,
+            "ops_definition": f"tcgen05.mma FLOPs issued: 2 group products x {T} BF16 term(s) x 8 K-steps of "
+                              "M = N = 128, K = 16 per (setting, high pattern, atom pair)",
+            "launches_per_step": la / args.steps,
+            "forward": {"kernel": "k_forward_tc", **part(f_ms)},
+            "adjoint": {"kernel": "k_adjoint_tc", **part(a_ms)},
+            "step_vs_plain_path": {
+                "ops_per_step": plain_ops, "ms_per_step": ms_step,
+                "frac": plain_ops / (ms_step / 1e3) / 1e12 / peak_alu,
+                "definition": "the plain FP32 method's work (6 m_s + 12 lane-ops per amplitude) at the FP32 lane "
+                              "peak, over the tensor-core step's time"}}
+
+
+def tc_against_fp32(args, inst, plan, psi, w, data, flush, ms_tc, grad, grad_w, loss):
+    """The FP32 plan on the same data: its evaluation time (same timing rules)
+    and the tensor-core result's distance from it at full size."""
+    import torch
+    from paper_2607_19577_b300 import qst
+    fp = qst.Plan(inst.n, inst.M, inst.K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits,
+                  chunk_qubits=args.chunk_qubits, max_bin_settings=args.max_bin_settings,
+                  fixed_rounds=args.fixed_rounds, phi_cache=args.phi_cache, precision=0)
+    stream = torch.cuda.current_stream()
+    p32, c32, l32, g32, gw32 = fp.evaluate(psi, w, data)
+    for _ in range(max(args.warmup, 1)):
+        flush.zero_()
+        fp.evaluate(psi, w, data, p_obs=p32, c_obs=c32, loss=l32, grad_psi=g32, grad_w=gw32)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        fp.evaluate(psi, w, data, p_obs=p32, c_obs=c32, loss=l32, grad_psi=g32, grad_w=gw32)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    fp.check()
+    ms32 = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    amps = inst.M * inst.K * inst.D
+    gn = g32.abs().amax(dim=1)
+    out = {"ms_per_step_fp32": ms32, "value_fp32": amps / (ms32 / 1e3), "ms_per_step_tc": ms_tc,
+           "tc_over_fp32_throughput": ms32 / ms_tc,
+           "grad_err_vs_fp32": float(((grad - g32).abs().amax(dim=1) / gn).max().item()),
+           "grad_w_err_vs_fp32": float(((grad_w - gw32).abs() / gw32.abs()).max().item()),
+           "loss_err_vs_fp32": float(abs(loss.item() - l32.item()) / abs(l32.item())),
+           "how": "the FP32 plan (precision 0) evaluated on the same data and stream right after, "
+                  f"{args.steps} steps, L2 flushed between steps; errors: per-atom max |d grad| / max |grad|, "
+                  "relative h and loss, tensor-core result against the FP32 one"}
+    fp.close()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2607_19577_b300 import qst, replicas, synth
@@ -336,7 +415,7 @@ def run_ours(args):
         tuned = [{"params": p, "ms": t} for p, t in table]
     plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, reg_bits=args.reg_bits, chunk_qubits=args.chunk_qubits,
                     max_bin_settings=args.max_bin_settings, fixed_rounds=args.fixed_rounds, phi_cache=args.phi_cache,
-                    norm_settings=M_all if args.shard else 0)
+                    norm_settings=M_all if args.shard else 0, precision=args.precision)
     p_obs = torch.empty(inst.nnz, dtype=torch.float32, device="cuda")
     c_obs = torch.empty_like(p_obs)
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -444,11 +523,14 @@ def run_ours(args):
                                   "(6 m_s + 12 lane-ops per amplitude) at the FP32 lane peak, over the whole "
                                   "step's time"}}
     kern = {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}
+    if args.precision > 0:
+        roofline = tc_roofline(args, inst, geo, stats, ms_step, fwd_ops + adj_ops, peaks, peak_alu)
+        roofline["vs_fp32"] = tc_against_fp32(args, inst, plan, psi, w, data, flush, ms_step, grad, grad_w, loss)
 
     # the same evaluation through qst_forward + qst_adjoint, whose adjoint
     # recomputes the rotations (the plain path's structure), for its roofline
     recompute = None
-    if cached and not args.shard and not wide:
+    if cached and not args.shard and not wide and args.precision == 0:
         def sep():
             plan.forward(psi, w, data, p_obs=p_obs, c_obs=c_obs, loss=loss)
             plan.adjoint(psi, w, data, c_obs, grad_psi=grad, grad_w=grad_w)
@@ -550,7 +632,10 @@ def run_ours(args):
                 "dtype": "f32",
                 "data": "synthetic (seeded; Pauli strings uniform, Porter-Thomas surrogate counts)",
                 "config": {"workload": args.workload, "n": n, "M": M, "K": K, "shots": int(inst.shots[0]),
-                           "nnz": int(inst.nnz), "precision_path": "plain FP32",
+                           "nnz": int(inst.nnz),
+                           "precision_path": "plain FP32" if args.precision == 0 else
+                           f"tensor cores: 6-qubit group products on tcgen05.mma kind::f16, the data split into "
+                           f"{args.precision} BF16 term(s), operators exact in BF16, FP32 accumulation in TMEM",
                            "step": "qst_evaluate: forward (stores the chunk transforms at the observed outcomes) + "
                                    "adjoint (inverse rotations of c .* the stored transforms)" if cached else
                                    "qst_evaluate: forward + adjoint that recomputes the rotations",

@@ -52,6 +52,8 @@ typedef enum qst_status {
 #define QST_DEV_BAD_CSR      2  /* row_ptr / outcome malformed (range, order) */
 #define QST_DEV_BAD_SHOTS    4  /* shots[s] == 0 for a non-empty row */
 #define QST_DEV_NONFINITE    8  /* the loss is NaN or Inf */
+#define QST_DEV_TIMEOUT     16  /* a tensor-core kernel's bounded wait on its own copies or MMAs ran out
+                                   (the kernel stopped issuing work and returned; results are invalid) */
 
 typedef struct qst_params {
     double eps;           /* epsilon of Eq. qst-loss (default 1e-8) */
@@ -77,6 +79,19 @@ typedef struct qst_params {
                              <= 16 GiB, off on the n = 20 path (whose adjoint recomputes the rotated
                              amplitudes unless asked).  qst_forward and qst_adjoint never use it.
                              Default -1. */
+    int precision;        /* arithmetic of the 12-qubit chunk transforms of two-round plans (n = 12..16
+                             with fixed_rounds resolving to 2).  0 = FP32 butterflies on the SIMT
+                             pipes (default).  1, 2, 3 = the transform as two dense products over
+                             groups of q = 6 qubits on the tensor cores (tcgen05.mma kind::f16):
+                             operators exact in BF16 (entries 0, +-1 before the 2^-m/2 scale), the
+                             data split into `precision` BF16 terms, FP32 accumulation in tensor
+                             memory.  Per amplitude and step the data error is <= 2^-8 precision
+                             times the amplitude (precision = 3 carries all 24 bits of FP32).
+                             precision > 0 on other plans: QST_ERR_UNSUPPORTED; outside 0..3:
+                             QST_ERR_INVALID_ARG.  The plan then also holds the 729 group operators
+                             (24 MB) and a K x nnz complex64 transform buffer: without the
+                             transform cache the adjoint first recomputes the transforms with the
+                             tensor-core forward. */
 } qst_params;
 
 typedef struct qst_plan_s *qst_plan;

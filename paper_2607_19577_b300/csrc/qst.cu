@@ -659,6 +659,8 @@ struct FwdArgs {
     const int *skip;         // optional device flag: when set, the launch does nothing
     int n, r, K;
     float2 *phi_obs = nullptr;  // optional [K][nnz]: the chunk transform of psi_k at the observed outcomes
+    const unsigned char *tc_ops = nullptr;  // tensor-core kernels: the 729 group operators
+    int *status = nullptr;                  // tensor-core kernels: QST_DEV_TIMEOUT
 };
 
 // Forward unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -803,6 +805,8 @@ struct AdjArgs {
     const float2 *phi_obs = nullptr;  // [K][nnz] from the forward (the cached adjoint reads it instead of psi)
     int64_t nnz = 0;
     const int *skip = nullptr;        // optional device flag: when set, the launch does nothing
+    const unsigned char *tc_ops = nullptr;  // tensor-core kernels: the 729 group operators
+    int *status = nullptr;                  // tensor-core kernels: QST_DEV_TIMEOUT
 };
 
 // Adjoint unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -1004,6 +1008,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_fixed.cuh"
 #include "qst_tworound.cuh"
 #include "qst_tworound_packed.cuh"
+#include "qst_tensorcore.cuh"
 #include "qst_single.cuh"
 #include "qst_iterate.cuh"
 
@@ -1028,6 +1033,8 @@ struct qst_plan_s {
     bool fx = false;         // 12-qubit chunks with fixed-position rounds (k_forward_fx / k_adjoint_fx)
     bool fx2 = false;        // 12-qubit chunks in two 6-bit rounds, two atoms per CTA (k_forward_2r / k_adjoint_2r)
     float2 *phi = nullptr;   // [K][nnz] transform cache of qst_evaluate (two-round plans, params.phi_cache)
+    bool cache_on = false;   // qst_evaluate passes phi from the forward to the adjoint
+    unsigned char *tc_ops = nullptr;  // precision > 0: the 729 six-qubit group operators (B operand layout)
     int wide_G = 0;
     float2 *wide_T = nullptr;    // [wide_G][K][D] intermediate (also the z buffer)
     double2 *wide_acc = nullptr; // [K][D] FP64 accumulator of G psi
@@ -1181,7 +1188,23 @@ void with_geo(int c, int ra, Fn &&fn) {
 // The plan's forward / adjoint chunk kernel over `units` work units per atom
 // (bins x high patterns): one CTA per unit and atom, or per unit and atom
 // pair for the two-round kernels.
-void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t st) {
+// Tensor-core kernels of a two-round plan with precision T = 1..3.
+template <int T>
+void launch_forward_tc(const FwdArgs &a, int grid, cudaStream_t st) {
+    if (a.phi_obs) k_forward_tc<T, true><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
+    else k_forward_tc<T, false><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
+}
+void launch_forward_units(qst_plan p, const FwdArgs &a0, int units, cudaStream_t st) {
+    FwdArgs a = a0;
+    a.tc_ops = p->tc_ops;
+    a.status = p->status;
+    if (p->fx2 && p->prm.precision > 0) {
+        const int grid = units * ((p->K + 1) / 2);
+        if (p->prm.precision == 1) launch_forward_tc<1>(a, grid, st);
+        else if (p->prm.precision == 2) launch_forward_tc<2>(a, grid, st);
+        else launch_forward_tc<3>(a, grid, st);
+        return;
+    }
     if (p->fx2) {
         if (a.phi_obs) k_forward_2r<true><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
         else k_forward_2r<false><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
@@ -1202,7 +1225,17 @@ void launch_forward_units(qst_plan p, const FwdArgs &a, int units, cudaStream_t 
         k_forward<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a);
     });
 }
-void launch_adjoint_units(qst_plan p, const AdjArgs &a, int units, cudaStream_t st) {
+void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t st) {
+    AdjArgs a = a0;
+    a.tc_ops = p->tc_ops;
+    a.status = p->status;
+    if (p->fx2 && p->prm.precision > 0) {  // adjoint_core supplies the transforms
+        const int grid = units * ((p->K + 1) / 2);
+        if (p->prm.precision == 1) k_adjoint_tc<1><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
+        else if (p->prm.precision == 2) k_adjoint_tc<2><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
+        else k_adjoint_tc<3><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
+        return;
+    }
     if (p->fx2 && a.phi_obs) {
         k_adjoint_2c<<<units * ((p->K + 1) / 2), k2T, k2c_smem().total, st>>>(a);
         return;
@@ -1361,6 +1394,7 @@ void qst_params_default(qst_params *p) {
     p->reg_bits = 0;
     p->fixed_rounds = -1;
     p->phi_cache = -1;
+    p->precision = 0;
 }
 
 const char *qst_status_string(qst_status s) {
@@ -1411,7 +1445,8 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
-    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 2 || prm.phi_cache < -1 || prm.phi_cache > 1) {
+    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 2 || prm.phi_cache < -1 || prm.phi_cache > 1 ||
+        prm.precision < 0 || prm.precision > 3) {
         delete p;
         return QST_ERR_INVALID_ARG;
     }
@@ -1440,6 +1475,11 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // the cached adjoint exists for the two-round kernels and the wide path's single-setting
     // 12-qubit-chunk kernels (n = 20)
     if (prm.phi_cache == 1 && !p->fx2 && !(wide && p->fx)) {
+        delete p;
+        return QST_ERR_UNSUPPORTED;
+    }
+    // the tensor-core chunk transforms exist for the two-round plans
+    if (prm.precision > 0 && !p->fx2) {
         delete p;
         return QST_ERR_UNSUPPORTED;
     }
@@ -1498,8 +1538,17 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // recomputes by default)
     if (!rc && nnz > 0 &&
         ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30)))) ||
-         (wide && p->fx && prm.phi_cache == 1)))
+         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0)))
         rc = dalloc(p, &p->phi, (size_t)K * nnz);
+    // with precision > 0 the buffer is also the tensor-core adjoint's input when the cache is off
+    p->cache_on = p->phi && !(prm.precision > 0 && prm.phi_cache == 0);
+    if (!rc && prm.precision > 0) {
+        rc = dalloc(p, &p->tc_ops, (size_t)kTcOps * kTcOpBytes);
+        if (!rc) {
+            k_tc_ops<<<kTcOps, 256>>>(reinterpret_cast<unsigned short *>(p->tc_ops));
+            if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = QST_ERR_CUDA;
+        }
+    }
     if (!rc) rc = dalloc(p, &p->it_state, 1);
     if (!rc && cudaMemset(p->it_state, 0, sizeof(IterState)) != cudaSuccess) rc = QST_ERR_CUDA;
     if (!rc) rc = dalloc(p, &p->it_c, nnz);
@@ -1530,6 +1579,17 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_adjoint_2c, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem().total);
             cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
         }
+        if (prm.precision > 0) {
+            cudaFuncSetAttribute(k_forward_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_forward_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_forward_tc<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_forward_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_forward_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_forward_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_adjoint_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_adjoint_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+            cudaFuncSetAttribute(k_adjoint_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
+        }
         if (cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
     }
     if (rc) {
@@ -1543,6 +1603,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
 qst_status qst_plan_destroy(qst_plan p) {
     if (!p) return QST_ERR_INVALID_ARG;
     cudaFree(p->phi);
+    cudaFree(p->tc_ops);
     cudaFree(p->plans);
     cudaFree(p->order);
     cudaFree(p->bins);
@@ -1731,6 +1792,32 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
         return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w, nullptr); });
     }
     const int units = p->nb_max << p->r;
+    if (p->fx2 && p->prm.precision > 0 && !phi_cache) {
+        // the tensor-core adjoint reads transforms: recompute them with the tensor-core forward
+        // (its w |.|^2 partials go to the plan's scratch and are not read)
+        FwdArgs f;
+        f.psi = a.psi;
+        f.w = w;
+        f.plans = p->plans;
+        f.order = p->order;
+        f.bins = p->bins;
+        f.n_bins = p->n_bins;
+        f.row_ptr = row_ptr;
+        f.outcome = outcome;
+        f.choff = p->choff;
+        f.ppart = p->ppart;
+        f.p_dense = nullptr;
+        f.nnz = p->nnz;
+        f.src_bin_stride = 0;
+        f.skip = skip;
+        f.n = p->n;
+        f.r = p->r;
+        f.K = p->K;
+        f.phi_obs = p->phi;
+        rc = launch(p, QST_KERNEL_FORWARD, st, [&] { launch_forward_units(p, f, units, st); });
+        if (rc) return rc;
+        a.phi_obs = p->phi;
+    }
     rc = launch(p, QST_KERNEL_ADJOINT, st, [&] {
         launch_adjoint_units(p, a, units, st);
     });
@@ -1770,8 +1857,8 @@ qst_status qst_evaluate(qst_plan p, const float *psi, const float *w, const uint
     cudaStream_t st = (cudaStream_t)stream;
     qst_status rc = prepare(p, basis, row_ptr, outcome, shots, st);
     if (!rc) rc = forward_core(p, psi, w, row_ptr, outcome, count, shots, p_obs, c_obs, loss, nullptr, nullptr, st,
-                               p->phi);
-    if (!rc) rc = adjoint_core(p, psi, w, row_ptr, outcome, c_obs, grad_psi, grad_w, st, p->phi);
+                               p->cache_on ? p->phi : nullptr);
+    if (!rc) rc = adjoint_core(p, psi, w, row_ptr, outcome, c_obs, grad_psi, grad_w, st, p->cache_on ? p->phi : nullptr);
     return rc;
 }
 
@@ -2457,6 +2544,7 @@ extern "C" qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz, cons
     if (!(prm.eps >= 0.0) || prm.norm_settings < 0 || prm.max_bin_settings < 0) return QST_ERR_INVALID_ARG;
     // always the per-setting-round kernels: a request for another family is refused
     if (prm.fixed_rounds != -1 && prm.fixed_rounds != 0) return QST_ERR_INVALID_ARG;
+    if (prm.precision != 0) return QST_ERR_UNSUPPORTED;  // the FP32 per-setting-round kernels only
     const int c = prm.chunk_qubits ? prm.chunk_qubits : (n < kMaxChunk ? n : kMaxChunk);
     if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
     const int r = n - c;

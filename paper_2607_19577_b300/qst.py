@@ -26,7 +26,7 @@ QST_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "unsupported size", 3: "CUDA error",
                 4: "out of device memory", 5: "device-side error"}
 DEV_BITS = {1: "bad basis code", 2: "malformed CSR counts", 4: "zero shots on a non-empty row",
-            8: "non-finite loss"}
+            8: "non-finite loss", 16: "tensor-core kernel wait timed out"}
 KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue", "refactor", "step",
                 "high", "tangent"]
 
@@ -39,7 +39,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm_settings", ctypes.c_int),
                 ("chunk_qubits", ctypes.c_int), ("max_bin_settings", ctypes.c_int),
                 ("validate", ctypes.c_int), ("reg_bits", ctypes.c_int), ("fixed_rounds", ctypes.c_int),
-                ("phi_cache", ctypes.c_int)]
+                ("phi_cache", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class _StepParams(ctypes.Structure):
@@ -162,7 +162,7 @@ class Plan:
     """Owns a qst_plan (device workspace for one problem shape)."""
 
     def __init__(self, n, M, K, nnz, eps=1e-8, norm_settings=0, chunk_qubits=0,
-                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=-1, phi_cache=-1):
+                 max_bin_settings=0, validate=True, reg_bits=0, fixed_rounds=-1, phi_cache=-1, precision=0):
         lib = load()
         prm = _Params()
         lib.qst_params_default(ctypes.byref(prm))
@@ -173,6 +173,9 @@ class Plan:
         prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(fixed_rounds)
         # phi_cache: qst_evaluate's transform cache (two-round plans): 1 on, 0 off, -1 automatic
         prm.phi_cache = int(phi_cache)
+        # precision (two-round plans): 0 FP32 butterflies; 1..3 tensor-core group
+        # products with the data split into that many BF16 terms
+        prm.precision = int(precision)
         h = ctypes.c_void_p()
         _check(lib.qst_plan_create(ctypes.byref(h), int(n), int(M), int(K), int(nnz), ctypes.byref(prm)),
                "qst_plan_create")
