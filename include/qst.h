@@ -369,17 +369,24 @@ qst_status qst_iterate_state(qst_plan plan, int *stopped, long long *oracle_call
 /*
  * Batched evaluation of many independent instances of uneven shape
  * (instances with different n, M, K and shots, e.g. 64 instances with n from
- * 6 to 14).  qst_batch_create makes one plan per instance (params shared).
- * qst_batch_evaluate runs every instance's qst_evaluate (qst_forward + qst_adjoint,
- * with the instance plan's transform cache where it has one); arguments
- * are HOST arrays of `count` DEVICE pointers, one per instance, with the
- * per-instance layouts of qst_forward / qst_adjoint (loss[i] -> double[1],
- * c_obs[i] -> float[nnz_i], grad_psi[i] -> complex64[K_i][2^n_i],
- * grad_w[i] -> float[K_i]).  The first call with a given set of pointers
- * captures all instances into one CUDA graph, with each instance on its own
- * forked stream so they run concurrently; later calls with the same pointers
- * replay it as a single graph launch on `stream` (the graph is captured on a
- * batch-owned stream in thread-local mode).
+ * 6 to 14).  qst_batch_create makes one plan per instance (params shared;
+ * unless params fixes max_bin_settings, every plan bins up to 96 settings,
+ * because the instances fill the GPU together: 12-qubit chunks then run the
+ * two-round kernels).  qst_batch_evaluate runs every instance's qst_evaluate
+ * (forward, then the adjoint with the instance plan's transform cache where
+ * it has one); arguments are HOST arrays of `count` DEVICE pointers, one per
+ * instance, with the per-instance layouts of qst_forward / qst_adjoint
+ * (loss[i] -> double[1], c_obs[i] -> float[nnz_i], grad_psi[i] ->
+ * complex64[K_i][2^n_i], grad_w[i] -> float[K_i]).  Each phase (packing,
+ * validation, forward chunk kernels, epilogue, loss, adjoint chunk kernels,
+ * reduction, h) is one launch over all instances per kernel family: the
+ * CTAs of every instance's grid in one grid, each CTA finding its instance
+ * from a table of CTA offsets; the families of a phase run on forked
+ * streams.  Batches with an instance on the wide path (n > 16) or on the
+ * tensor cores run every instance's qst_evaluate on forked streams instead.
+ * The first call with a given set of pointers captures the launches into
+ * one CUDA graph (on a batch-owned stream in thread-local mode); later calls
+ * with the same pointers replay it as a single graph launch on `stream`.
  * qst_batch_plan returns instance i's plan (for qst_plan_status etc.).
  */
 typedef struct qst_batch_s *qst_batch;

@@ -33,6 +33,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -243,12 +244,33 @@ __device__ __forceinline__ void stage_bin(const Bin &b, uint32_t f, int nf, cons
 
 // ----------------------------------------------------------------- kernels
 
+// w 2^-m |z|^2 with every rounding fixed in the source (fma(re, re, im * im),
+// then the scale), so kernels that share the expression give the same bits
+// whatever contractions the compiler would choose in each.
+__device__ __forceinline__ float scaled_abs2(float sc, float2 z) {
+    return __fmul_rn(sc, __fmaf_rn(z.x, z.x, __fmul_rn(z.y, z.y)));
+}
+
+// Multi-instance launches (qst_batch): the CTAs of several instances' grids
+// in one launch.  start[i] is the first CTA of instance i (ascending, start[0]
+// = 0); a CTA finds its instance by binary search and runs the instance's
+// kernel body with its CTA index within that instance's grid.
+__device__ __forceinline__ int multi_find(const int *__restrict__ start, int count, int bid) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Descriptor packing (Sec. IV: Pauli strings) and setting binning: one block.
-__global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis, int M, int n, int c, int r,
+__device__ __forceinline__ void pack_body(const uint8_t *__restrict__ basis, int M, int n, int c, int r,
                                                int smax, int areg, SetPlan *__restrict__ plans,
                                                int32_t *__restrict__ order,
                                                Bin *__restrict__ bins, int *__restrict__ n_bins,
-                                               int *__restrict__ status) {
+                                               int *__restrict__ status, const int cta) {
     __shared__ int hist[kMaxKeys], running[kMaxKeys];
     __shared__ int wcnt[32][kMaxKeys];
     const int tid = threadIdx.x;
@@ -386,14 +408,21 @@ __global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis
         __syncthreads();
     }
 }
+__global__ void __launch_bounds__(1024) k_pack(const uint8_t *__restrict__ basis, int M, int n, int c, int r,
+                                               int smax, int areg, SetPlan *__restrict__ plans,
+                                               int32_t *__restrict__ order,
+                                               Bin *__restrict__ bins, int *__restrict__ n_bins,
+                                               int *__restrict__ status) {
+    pack_body(basis, M, n, c, r, smax, areg, plans, order, bins, n_bins, status, blockIdx.x);
+}
 
 // CSR validation and per-(setting, high pattern) offsets of the observed
 // outcomes (outcomes are sorted, so each high pattern is a contiguous range).
 // One warp per setting.  A malformed row is flagged and treated as empty.
-__global__ void k_validate(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ outcome,
+__device__ __forceinline__ void validate_body(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ outcome,
                            const uint32_t *__restrict__ shots, int M, int64_t nnz, int n, int c, int r,
-                           int validate, int32_t *__restrict__ choff, int *__restrict__ status) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                           int validate, int32_t *__restrict__ choff, int *__restrict__ status, const int cta) {
+    const int gw = (cta * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (gw >= M) return;
     const int s = gw;
@@ -427,6 +456,11 @@ __global__ void k_validate(const int64_t *__restrict__ row_ptr, const uint32_t *
         }
         co[f] = (int32_t)(a - lo);
     }
+}
+__global__ void k_validate(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ outcome,
+                           const uint32_t *__restrict__ shots, int M, int64_t nnz, int n, int c, int r,
+                           int validate, int32_t *__restrict__ choff, int *__restrict__ status) {
+    validate_body(row_ptr, outcome, shots, M, nnz, n, c, r, validate, choff, status, blockIdx.x);
 }
 
 // Compile-time geometry of a chunk of 2^C amplitudes.
@@ -668,7 +702,7 @@ struct FwdArgs {
 // outcomes in chunk f, written to this atom's slice of the partial buffer.
 // The next setting's outcome indices are prefetched with cp.async.
 template <int C, int RA>
-__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
+__device__ __forceinline__ void forward_body(const FwdArgs a, const int cta) {
     using G = Geo<C, RA>;
     constexpr SmemPlan sp = smem_plan(C, false);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -680,7 +714,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem + sp.lut);
     __shared__ int total_sm;
     const uint32_t tid = threadIdx.x;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int k = unit % a.K;
     const int rest = unit / a.K;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -724,14 +758,14 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
         for (int j = tid; j < mt.cnt; j += G::T) {
             const uint32_t u = (j < kStage ? st[j] : outcome[mt.lo + j]) & cmask;
             const float2 ph = lds2(work + (phys(u) << 3));
-            pk[mt.lo + j] = sc * (ph.x * ph.x + ph.y * ph.y);
+            pk[mt.lo + j] = scaled_abs2(sc, ph);
         }
         if (a.p_dense) {
             const int s = a.order[b.start + si];
             float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
             for (uint32_t u = tid; u <= cmask; u += G::T) {
                 const float2 ph = lds2(work + (phys(u) << 3));
-                atomicAdd(pd + u, sc * (ph.x * ph.x + ph.y * ph.y));
+                atomicAdd(pd + u, scaled_abs2(sc, ph));
             }
         }
         if (si + 1 < bcount) build_lut<G::TB>(plans_sm[si + 1], lut + ((si + 1) & 1) * LUTW, tid, G::T);
@@ -739,20 +773,30 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
     }
     cp_async_wait0();
 }
+template <int C, int RA>
+__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward(const FwdArgs a) {
+    forward_body<C, RA>(a, blockIdx.x);
+}
+template <int C, int RA>
+__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_forward_multi(const FwdArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const FwdArgs a = args[i];
+    forward_body<C, RA>(a, (int)blockIdx.x - start[i]);
+}
 
 // Forward epilogue, one warp per setting: p = sum_k of the atom partials
 // (fixed order), pi = p / B, c = pihat / (pi + eps) and the loss terms
 // -pihat log(pi + eps) (Eqs. qst-loss, likelihood-ratio-vector).  Per-block
 // FP64 loss partials are summed by k_loss.
-__global__ void __launch_bounds__(256) k_fwd_epilogue(const float *__restrict__ ppart, const int64_t *__restrict__ row_ptr,
+__device__ __forceinline__ void epilogue_body(const float *__restrict__ ppart, const int64_t *__restrict__ row_ptr,
                                                       const uint32_t *__restrict__ count,
                                                       const uint32_t *__restrict__ shots,
                                                       int M, int K, int64_t nnz, float invB, float eps,
                                                       float *__restrict__ p_obs, float *__restrict__ c_obs,
-                                                      double *__restrict__ loss_part, const int *skip) {
+                                                      double *__restrict__ loss_part, const int *skip, const int cta) {
     if (skip && *skip) return;
     __shared__ double red[kRedMax];
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int s = (cta * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     double lsum = 0.0;
     if (s < M) {
@@ -764,16 +808,24 @@ __global__ void __launch_bounds__(256) k_fwd_epilogue(const float *__restrict__ 
             for (int64_t i = lo + lane; i < hi; i += 32) {
                 float p = 0.f;
                 for (int k = 0; k < K; ++k) p += ppart[(size_t)k * nnz + i];
-                const float pi = p * invB;
-                const float pihat = (float)count[i] * invB / ns;
-                if (c_obs) c_obs[i] = pihat / (pi + eps);
+                const float den = __fadd_rn(__fmul_rn(p, invB), eps);  // pi + eps
+                const float pihat = __fdiv_rn(__fmul_rn((float)count[i], invB), ns);
+                if (c_obs) c_obs[i] = __fdiv_rn(pihat, den);
                 if (p_obs) p_obs[i] = p;
-                lsum -= (double)pihat * (double)logf(pi + eps);
+                lsum = fma(-(double)pihat, (double)logf(den), lsum);
             }
         }
     }
     const double t = block_sum<double>(lsum, red);
-    if (threadIdx.x == 0) loss_part[blockIdx.x] = t;
+    if (threadIdx.x == 0) loss_part[cta] = t;
+}
+__global__ void __launch_bounds__(256) k_fwd_epilogue(const float *__restrict__ ppart, const int64_t *__restrict__ row_ptr,
+                                                      const uint32_t *__restrict__ count,
+                                                      const uint32_t *__restrict__ shots,
+                                                      int M, int K, int64_t nnz, float invB, float eps,
+                                                      float *__restrict__ p_obs, float *__restrict__ c_obs,
+                                                      double *__restrict__ loss_part, const int *skip) {
+    epilogue_body(ppart, row_ptr, count, shots, M, K, nnz, invB, eps, p_obs, c_obs, loss_part, skip, blockIdx.x);
 }
 
 // d_k = -grad_k + w_k grad_w_k psi_k = w_k (I - psi_k psi_k^*) G psi_k
@@ -816,7 +868,7 @@ struct AdjArgs {
 // setting's (outcome, c) pairs are prefetched with cp.async and scattered into
 // the dense c buffer at the end of the current setting.
 template <int C, int RA>
-__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
+__device__ __forceinline__ void adjoint_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
     using G = Geo<C, RA>;
     constexpr SmemPlan sp = smem_plan(C, true);
@@ -831,7 +883,7 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem + sp.lut);
     __shared__ int total_sm;
     const uint32_t tid = threadIdx.x;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int k = unit % a.K;
     const int rest = unit / a.K;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -894,8 +946,8 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
         L.walk([&](auto ic, uint32_t x) {
             constexpr int i = decltype(ic)::value;
             const float cc = *reinterpret_cast<const float *>(cdb + (x >> 1));
-            v[i].x *= cc;
-            v[i].y *= cc;
+            v[i].x = __fmul_rn(v[i].x, cc);  // not contracted into the butterflies that follow
+            v[i].y = __fmul_rn(v[i].y, cc);
         });
         for (int j = nr - 1;; --j) {  // one butterfly site
             butterfly_inv<G::A>(v, L.xyf, L.yf);
@@ -922,18 +974,28 @@ __global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
 #pragma unroll
     for (int i = 0; i < G::E; ++i) zo[tid + (i << G::TB)] = z[i];
 }
+template <int C, int RA>
+__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint(const AdjArgs a) {
+    adjoint_body<C, RA>(a, blockIdx.x);
+}
+template <int C, int RA>
+__global__ void __launch_bounds__(Geo<C, RA>::T, 2) k_adjoint_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const AdjArgs a = args[i];
+    adjoint_body<C, RA>(a, (int)blockIdx.x - start[i]);
+}
 
 // grad_k[f, l] = -(w_k / B) sum_bins (U_h^* z_{bin,k})[f, l]: the high-bit
 // conjugate-transposed factors per bin, Kahan-compensated sum over bins.
 template <int R>
-__global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf, const Bin *__restrict__ bins,
+__device__ __forceinline__ void reduce_body(const float2 *__restrict__ zbuf, const Bin *__restrict__ bins,
                                                 const int *__restrict__ n_bins, const float *__restrict__ w,
                                                 const float2 *__restrict__ psi, float2 *__restrict__ grad,
                                                 double *__restrict__ hdot, int n, int c, int K, float invB,
-                                                const int *skip) {
+                                                const int *skip, const int cta) {
     if (skip && *skip) return;
     constexpr int F = 1 << R;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t idx = (int64_t)cta * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)K << c;
     if (idx >= total) return;
     const int k = (int)(idx >> c);
@@ -969,28 +1031,40 @@ __global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf,
     for (int f = 0; f < F; ++f) {
         gp[(size_t)f << c] = make_float2(sc * acc[f].x, sc * acc[f].y);
         const float2 q = pp[(size_t)f << c];
-        hd += (double)q.x * (double)acc[f].x + (double)q.y * (double)acc[f].y;
+        hd = fma((double)q.y, (double)acc[f].y, fma((double)q.x, (double)acc[f].x, hd));
     }
     hdot[idx] = hd;
+}
+template <int R>
+__global__ void __launch_bounds__(256) k_reduce(const float2 *__restrict__ zbuf, const Bin *__restrict__ bins,
+                                                const int *__restrict__ n_bins, const float *__restrict__ w,
+                                                const float2 *__restrict__ psi, float2 *__restrict__ grad,
+                                                double *__restrict__ hdot, int n, int c, int K, float invB,
+                                                const int *skip) {
+    reduce_body<R>(zbuf, bins, n_bins, w, psi, grad, hdot, n, c, K, invB, skip, blockIdx.x);
 }
 
 // grad_w_k = -h_k with h_k = a(psi_k)^T c = <psi_k | G psi_k> (Eqs. weight-gradient,
 // atom-response): the FP64 sum of the reduction kernel's per-thread partials.
-__global__ void __launch_bounds__(256) k_hsum(const double *__restrict__ hdot, int c, float invB,
-                                              float *__restrict__ grad_w, const int *skip) {
+__device__ __forceinline__ void hsum_body(const double *__restrict__ hdot, int c, float invB,
+                                              float *__restrict__ grad_w, const int *skip, const int cta) {
     if (skip && *skip) return;
     __shared__ double red[kRedMax];
-    const int k = blockIdx.x;
+    const int k = cta;
     const double *hp = hdot + ((size_t)k << c);
     double s = 0.0;
     for (int u = threadIdx.x; u < (1 << c); u += blockDim.x) s += hp[u];
     const double t = block_sum<double>(s, red);
     if (threadIdx.x == 0) grad_w[k] = (float)(-t * (double)invB);
 }
+__global__ void __launch_bounds__(256) k_hsum(const double *__restrict__ hdot, int c, float invB,
+                                              float *__restrict__ grad_w, const int *skip) {
+    hsum_body(hdot, c, invB, grad_w, skip, blockIdx.x);
+}
 
 // loss = sum of the forward epilogue's per-block partial sums (FP64, fixed order).
-__global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_part, int parts,
-                                              double *__restrict__ loss, int *__restrict__ status, const int *skip) {
+__device__ __forceinline__ void loss_body(const double *__restrict__ loss_part, int parts,
+                                              double *__restrict__ loss, int *__restrict__ status, const int *skip, const int cta) {
     if (skip && *skip) return;
     __shared__ double red[kRedMax];
     double s = 0.0;
@@ -1000,6 +1074,10 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
         if (loss) *loss = t;
         if (!isfinite(t)) atomicOr(status, QST_DEV_NONFINITE);
     }
+}
+__global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_part, int parts,
+                                              double *__restrict__ loss, int *__restrict__ status, const int *skip) {
+    loss_body(loss_part, parts, loss, status, skip, blockIdx.x);
 }
 
 #include "qst_update.cuh"
@@ -2612,6 +2690,131 @@ extern "C" qst_status qst_adjoint_noalloc(int n, int M, int K, int64_t nnz, cons
 // instance's forward + adjoint onto its own stream, so the instances run
 // concurrently and the whole batch is one graph launch.
 
+namespace {
+
+// Argument records of qst_batch_evaluate's multi-instance launches (one per
+// instance and launch; the unit kernels take FwdArgs / AdjArgs).
+struct PackArgs {
+    const uint8_t *basis;
+    int M, n, c, r, smax, areg;
+    SetPlan *plans;
+    int32_t *order;
+    Bin *bins;
+    int *n_bins, *status;
+};
+struct ValArgs {
+    const int64_t *row_ptr;
+    const uint32_t *outcome, *shots;
+    int M;
+    int64_t nnz;
+    int n, c, r, validate;
+    int32_t *choff;
+    int *status;
+};
+struct EpiArgs {
+    const float *ppart;
+    const int64_t *row_ptr;
+    const uint32_t *count, *shots;
+    int M, K;
+    int64_t nnz;
+    float invB, eps;
+    float *c_obs;
+    double *loss_part;
+};
+struct LossArgs {
+    const double *loss_part;
+    int parts;
+    double *loss;
+    int *status;
+};
+struct RedArgs {
+    const float2 *zbuf;
+    const Bin *bins;
+    const int *n_bins;
+    const float *w;
+    const float2 *psi;
+    float2 *grad;
+    double *hdot;
+    int n, c, K, r;
+    float invB;
+};
+struct HsumArgs {
+    const double *hdot;
+    int c;
+    float invB;
+    float *grad_w;
+};
+
+__global__ void __launch_bounds__(1024) k_pack_multi(const PackArgs *__restrict__ args) {
+    const PackArgs a = args[blockIdx.x];
+    pack_body(a.basis, a.M, a.n, a.c, a.r, a.smax, a.areg, a.plans, a.order, a.bins, a.n_bins, a.status, 0);
+}
+__global__ void __launch_bounds__(256) k_validate_multi(const ValArgs *__restrict__ args, const int *__restrict__ start,
+                                                        int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const ValArgs a = args[i];
+    validate_body(a.row_ptr, a.outcome, a.shots, a.M, a.nnz, a.n, a.c, a.r, a.validate, a.choff, a.status,
+                  (int)blockIdx.x - start[i]);
+}
+__global__ void __launch_bounds__(256) k_fwd_epilogue_multi(const EpiArgs *__restrict__ args,
+                                                            const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const EpiArgs a = args[i];
+    epilogue_body(a.ppart, a.row_ptr, a.count, a.shots, a.M, a.K, a.nnz, a.invB, a.eps, nullptr, a.c_obs,
+                  a.loss_part, nullptr, (int)blockIdx.x - start[i]);
+}
+__global__ void __launch_bounds__(256) k_loss_multi(const LossArgs *__restrict__ args) {
+    const LossArgs a = args[blockIdx.x];
+    loss_body(a.loss_part, a.parts, a.loss, a.status, nullptr, 0);
+}
+__global__ void __launch_bounds__(256) k_reduce_multi(const RedArgs *__restrict__ args, const int *__restrict__ start,
+                                                      int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const RedArgs a = args[i];
+    const int cta = (int)blockIdx.x - start[i];
+    switch (a.r) {
+        case 0: reduce_body<0>(a.zbuf, a.bins, a.n_bins, a.w, a.psi, a.grad, a.hdot, a.n, a.c, a.K, a.invB, nullptr, cta); break;
+        case 1: reduce_body<1>(a.zbuf, a.bins, a.n_bins, a.w, a.psi, a.grad, a.hdot, a.n, a.c, a.K, a.invB, nullptr, cta); break;
+        case 2: reduce_body<2>(a.zbuf, a.bins, a.n_bins, a.w, a.psi, a.grad, a.hdot, a.n, a.c, a.K, a.invB, nullptr, cta); break;
+        case 3: reduce_body<3>(a.zbuf, a.bins, a.n_bins, a.w, a.psi, a.grad, a.hdot, a.n, a.c, a.K, a.invB, nullptr, cta); break;
+        default: reduce_body<4>(a.zbuf, a.bins, a.n_bins, a.w, a.psi, a.grad, a.hdot, a.n, a.c, a.K, a.invB, nullptr, cta); break;
+    }
+}
+__global__ void __launch_bounds__(256) k_hsum_multi(const HsumArgs *__restrict__ args, const int *__restrict__ start,
+                                                    int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const HsumArgs a = args[i];
+    hsum_body(a.hdot, a.c, a.invB, a.grad_w, nullptr, (int)blockIdx.x - start[i]);
+}
+
+// Chunk-kernel family of a plan: the multi-instance forward / adjoint
+// launches group instances by it (same kernel, block and shared memory).
+enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3 };  // >= 0: generic kernels, 100 c + A
+int plan_family(const qst_plan_s *p) {
+    if (p->fx2) return p->cache_on ? kFam2rCache : kFam2r;
+    if (p->fx) return kFamFx;
+    return 100 * p->c + p->A;
+}
+// CTAs of one instance's forward / adjoint grid
+int64_t plan_unit_ctas(const qst_plan_s *p) {
+    const int64_t units = (int64_t)p->nb_max << p->r;
+    return units * (p->fx2 ? (p->K + 1) / 2 : p->K);
+}
+
+constexpr int kBatchStreams = 16;
+
+enum BatchPhase { kPhPack, kPhValidate, kPhForward, kPhEpilogue, kPhLoss, kPhAdjoint, kPhReduce, kPhHsum, kPhases };
+
+// One multi-instance launch: its grid, and where its argument records and
+// CTA starts sit in the batch's device argument buffer.
+struct BatchLaunch {
+    int phase, family;
+    int grid, count;
+    size_t args_off, start_off;
+};
+
+}  // namespace
+
 struct qst_batch_s {
     int count = 0;
     std::vector<qst_plan> plans;
@@ -2621,11 +2824,11 @@ struct qst_batch_s {
     cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy default stream)
     cudaGraphExec_t exec = nullptr;
     std::vector<const void *> key;  // buffers the graph was captured with
+    bool multi = false;             // every plan has a multi-instance kernel family
+    unsigned char *dev_args = nullptr;
+    size_t dev_bytes = 0;
+    std::vector<BatchLaunch> launches;
 };
-
-namespace {
-constexpr int kBatchStreams = 16;
-}
 
 extern "C" qst_status qst_batch_destroy(qst_batch b) {
     if (!b) return QST_ERR_INVALID_ARG;
@@ -2637,9 +2840,33 @@ extern "C" qst_status qst_batch_destroy(qst_batch b) {
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->start) cudaEventDestroy(b->start);
     if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->dev_args);
     delete b;
     return QST_OK;
 }
+
+namespace {
+// Dynamic shared memory limits of the multi-instance chunk kernels of a family.
+void set_family_attrs(int fam) {
+    if (fam == kFam2rCache || fam == kFam2r) {
+        cudaFuncSetAttribute(k_forward_2r_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+        cudaFuncSetAttribute(k_forward_2r_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+        cudaFuncSetAttribute(k_adjoint_2c_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem().total);
+        cudaFuncSetAttribute(k_adjoint_2r_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+    } else if (fam == kFamFx) {
+        cudaFuncSetAttribute(k_forward_fx_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(false).total);
+        cudaFuncSetAttribute(k_adjoint_fx_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
+    } else {
+        with_geo(fam / 100, fam % 100, [](auto cc, auto ra) {
+            constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+            cudaFuncSetAttribute(k_forward_multi<C, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_plan(C, false).total);
+            cudaFuncSetAttribute(k_adjoint_multi<C, RA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_plan(C, true).total);
+        });
+    }
+}
+}  // namespace
 
 extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, const int *M, const int *K,
                                        const int64_t *nnz, const qst_params *params) {
@@ -2649,11 +2876,29 @@ extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, 
     if (!b) return QST_ERR_NO_MEMORY;
     b->count = count;
     b->plans.assign(count, nullptr);
+    // The instances share the GPU, so no plan needs small bins to fill it alone:
+    // unless the caller fixes max_bin_settings, every plan bins up to kMaxBin
+    // settings (12-qubit chunks then run the two-round kernels).
+    qst_params prm;
+    qst_params_default(&prm);
+    if (params) prm = *params;
+    if (!params || params->max_bin_settings == 0) prm.max_bin_settings = kMaxBin;
     for (int i = 0; i < count; ++i) {
-        const qst_status rc = qst_plan_create(&b->plans[i], n[i], M[i], K[i], nnz[i], params);
+        const qst_status rc = qst_plan_create(&b->plans[i], n[i], M[i], K[i], nnz[i], &prm);
         if (rc) {
             qst_batch_destroy(b);
             return rc;
+        }
+    }
+    // multi-instance launches for every plan off the wide path and off the tensor cores
+    b->multi = true;
+    for (auto p : b->plans)
+        if (p->wide || p->prm.precision > 0) b->multi = false;
+    if (b->multi) {
+        for (auto p : b->plans) set_family_attrs(plan_family(p));
+        if (cudaGetLastError() != cudaSuccess) {
+            qst_batch_destroy(b);
+            return QST_ERR_CUDA;
         }
     }
     const int ns = count < kBatchStreams ? count : kBatchStreams;
@@ -2680,6 +2925,226 @@ extern "C" qst_status qst_batch_plan(qst_batch b, int i, qst_plan *plan) {
     return QST_OK;
 }
 
+namespace {
+// Host-side image of the device argument buffer (16-byte aligned arrays).
+struct ArgImage {
+    std::vector<unsigned char> bytes;
+    template <typename T>
+    size_t put(const std::vector<T> &v) {
+        const size_t off = (bytes.size() + 15) & ~(size_t)15;
+        bytes.resize(off + v.size() * sizeof(T));
+        if (!v.empty()) memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+};
+
+// Argument records and launches of one batch evaluation.  Per phase, one
+// launch per kernel family; within a family the instances with the most
+// settings per bin come first, so their long CTAs start first.
+qst_status batch_build(qst_batch b, const float *const *psi, const float *const *w, const uint8_t *const *basis,
+                       const int64_t *const *row_ptr, const uint32_t *const *outcome, const uint32_t *const *count,
+                       const uint32_t *const *shots, double *const *loss, float *const *c_obs,
+                       float *const *grad_psi, float *const *grad_w) {
+    ArgImage img;
+    b->launches.clear();
+    const int N = b->count;
+    auto add = [&](int phase, int family, const std::vector<int> &grid_of, size_t args_off) {
+        std::vector<int> start(grid_of.size() + 1, 0);
+        for (size_t i = 0; i < grid_of.size(); ++i) start[i + 1] = start[i] + grid_of[i];
+        BatchLaunch L;
+        L.phase = phase;
+        L.family = family;
+        L.grid = start.back();
+        L.count = (int)grid_of.size();
+        L.args_off = args_off;
+        L.start_off = img.put(start);
+        if (L.grid > 0) b->launches.push_back(L);
+    };
+    {
+        std::vector<PackArgs> a(N);
+        std::vector<int> g(N, 1);
+        for (int i = 0; i < N; ++i) {
+            const qst_plan p = b->plans[i];
+            a[i] = PackArgs{basis[i], p->M, p->n, p->c, p->r, p->smax, p->A, p->plans, p->order, p->bins,
+                            p->n_bins, p->status};
+        }
+        add(kPhPack, 0, g, img.put(a));
+    }
+    {
+        std::vector<ValArgs> a(N);
+        std::vector<int> g(N);
+        for (int i = 0; i < N; ++i) {
+            const qst_plan p = b->plans[i];
+            a[i] = ValArgs{row_ptr[i], outcome[i], shots[i], p->M, p->nnz, p->n, p->c, p->r, p->prm.validate,
+                           p->choff, p->status};
+            g[i] = (p->M + 7) / 8;
+        }
+        add(kPhValidate, 0, g, img.put(a));
+    }
+    // kernel families, instances ordered by settings per bin (descending)
+    std::vector<int> fams;
+    for (auto p : b->plans) {
+        const int f = plan_family(p);
+        if (std::find(fams.begin(), fams.end(), f) == fams.end()) fams.push_back(f);
+    }
+    std::vector<std::vector<int>> members(fams.size());
+    for (size_t fi = 0; fi < fams.size(); ++fi) {
+        for (int i = 0; i < N; ++i)
+            if (plan_family(b->plans[i]) == fams[fi]) members[fi].push_back(i);
+        std::stable_sort(members[fi].begin(), members[fi].end(),
+                         [&](int x, int y) { return b->plans[x]->smax > b->plans[y]->smax; });
+    }
+    for (size_t fi = 0; fi < fams.size(); ++fi) {
+        std::vector<FwdArgs> a;
+        std::vector<int> g;
+        for (int i : members[fi]) {
+            const qst_plan p = b->plans[i];
+            FwdArgs f;
+            f.psi = reinterpret_cast<const float2 *>(psi[i]);
+            f.w = w[i];
+            f.plans = p->plans;
+            f.order = p->order;
+            f.bins = p->bins;
+            f.n_bins = p->n_bins;
+            f.row_ptr = row_ptr[i];
+            f.outcome = outcome[i];
+            f.choff = p->choff;
+            f.ppart = p->ppart;
+            f.p_dense = nullptr;
+            f.nnz = p->nnz;
+            f.src_bin_stride = 0;
+            f.skip = nullptr;
+            f.n = p->n;
+            f.r = p->r;
+            f.K = p->K;
+            f.phi_obs = p->cache_on ? p->phi : nullptr;
+            f.tc_ops = p->tc_ops;
+            f.status = p->status;
+            a.push_back(f);
+            g.push_back((int)plan_unit_ctas(p));
+        }
+        add(kPhForward, fams[fi], g, img.put(a));
+    }
+    {
+        std::vector<EpiArgs> a(N);
+        std::vector<LossArgs> la(N);
+        std::vector<int> g(N), one(N, 1);
+        for (int i = 0; i < N; ++i) {
+            const qst_plan p = b->plans[i];
+            a[i] = EpiArgs{p->ppart, row_ptr[i], count[i], shots[i], p->M, p->K, p->nnz, 1.0f / (float)p->B,
+                           (float)p->prm.eps, c_obs[i], p->loss_part};
+            g[i] = p->loss_parts;
+            la[i] = LossArgs{p->loss_part, p->loss_parts, loss[i], p->status};
+        }
+        add(kPhEpilogue, 0, g, img.put(a));
+        add(kPhLoss, 0, one, img.put(la));
+    }
+    for (size_t fi = 0; fi < fams.size(); ++fi) {
+        std::vector<AdjArgs> a;
+        std::vector<int> g;
+        for (int i : members[fi]) {
+            const qst_plan p = b->plans[i];
+            AdjArgs d;
+            d.psi = reinterpret_cast<const float2 *>(psi[i]);
+            d.plans = p->plans;
+            d.order = p->order;
+            d.bins = p->bins;
+            d.n_bins = p->n_bins;
+            d.row_ptr = row_ptr[i];
+            d.outcome = outcome[i];
+            d.c_obs = c_obs[i];
+            d.choff = p->choff;
+            d.zbuf = p->zbuf;
+            d.src_bin_stride = 0;
+            d.n = p->n;
+            d.r = p->r;
+            d.K = p->K;
+            d.phi_obs = p->cache_on ? p->phi : nullptr;
+            d.nnz = p->nnz;
+            d.skip = nullptr;
+            d.tc_ops = p->tc_ops;
+            d.status = p->status;
+            a.push_back(d);
+            g.push_back((int)plan_unit_ctas(p));
+        }
+        add(kPhAdjoint, fams[fi], g, img.put(a));
+    }
+    {
+        std::vector<RedArgs> a(N);
+        std::vector<HsumArgs> h(N);
+        std::vector<int> g(N), gk(N);
+        for (int i = 0; i < N; ++i) {
+            const qst_plan p = b->plans[i];
+            const float invB = 1.0f / (float)p->B;
+            a[i] = RedArgs{p->zbuf, p->bins, p->n_bins, w[i], reinterpret_cast<const float2 *>(psi[i]),
+                           reinterpret_cast<float2 *>(grad_psi[i]), p->hdot, p->n, p->c, p->K, p->r, invB};
+            g[i] = (int)((((int64_t)p->K << p->c) + 255) / 256);
+            h[i] = HsumArgs{p->hdot, p->c, invB, grad_w[i]};
+            gk[i] = p->K;
+        }
+        add(kPhReduce, 0, g, img.put(a));
+        add(kPhHsum, 0, gk, img.put(h));
+    }
+    if (img.bytes.size() > b->dev_bytes) {
+        cudaFree(b->dev_args);
+        b->dev_args = nullptr;
+        b->dev_bytes = 0;
+        if (cudaMalloc(&b->dev_args, img.bytes.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return QST_ERR_NO_MEMORY;
+        }
+        b->dev_bytes = img.bytes.size();
+    }
+    if (cudaMemcpy(b->dev_args, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return QST_ERR_CUDA;
+    return QST_OK;
+}
+
+void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
+    const unsigned char *base = b->dev_args;
+    const int *start = reinterpret_cast<const int *>(base + L.start_off);
+    const void *args = base + L.args_off;
+    const int grid = L.grid, cnt = L.count, fam = L.family;
+    switch (L.phase) {
+        case kPhPack: k_pack_multi<<<grid, 1024, 0, st>>>(static_cast<const PackArgs *>(args)); break;
+        case kPhValidate:
+            k_validate_multi<<<grid, 256, 0, st>>>(static_cast<const ValArgs *>(args), start, cnt);
+            break;
+        case kPhEpilogue:
+            k_fwd_epilogue_multi<<<grid, 256, 0, st>>>(static_cast<const EpiArgs *>(args), start, cnt);
+            break;
+        case kPhLoss: k_loss_multi<<<grid, 256, 0, st>>>(static_cast<const LossArgs *>(args)); break;
+        case kPhReduce: k_reduce_multi<<<grid, 256, 0, st>>>(static_cast<const RedArgs *>(args), start, cnt); break;
+        case kPhHsum: k_hsum_multi<<<grid, 256, 0, st>>>(static_cast<const HsumArgs *>(args), start, cnt); break;
+        case kPhForward: {
+            const FwdArgs *a = static_cast<const FwdArgs *>(args);
+            if (fam == kFam2rCache) k_forward_2r_multi<true><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r) k_forward_2r_multi<false><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
+            else if (fam == kFamFx) k_forward_fx_multi<<<grid, kFxT, fx_smem(false).total, st>>>(a, start, cnt);
+            else
+                with_geo(fam / 100, fam % 100, [&](auto cc, auto ra) {
+                    constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+                    k_forward_multi<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, false).total, st>>>(a, start, cnt);
+                });
+            break;
+        }
+        case kPhAdjoint: {
+            const AdjArgs *a = static_cast<const AdjArgs *>(args);
+            if (fam == kFam2rCache) k_adjoint_2c_multi<<<grid, k2T, k2c_smem().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r) k_adjoint_2r_multi<<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
+            else if (fam == kFamFx) k_adjoint_fx_multi<<<grid, kFxT, fx_smem(true).total, st>>>(a, start, cnt);
+            else
+                with_geo(fam / 100, fam % 100, [&](auto cc, auto ra) {
+                    constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
+                    k_adjoint_multi<C, RA><<<grid, Geo<C, RA>::T, smem_plan(C, true).total, st>>>(a, start, cnt);
+                });
+            break;
+        }
+        default: break;
+    }
+}
+}  // namespace
+
 extern "C" qst_status qst_batch_evaluate(qst_batch b, const float *const *psi, const float *const *w,
                                          const uint8_t *const *basis, const int64_t *const *row_ptr,
                                          const uint32_t *const *outcome, const uint32_t *const *count,
@@ -2703,6 +3168,11 @@ extern "C" qst_status qst_batch_evaluate(qst_batch b, const float *const *psi, c
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
         }
+        if (b->multi) {
+            const qst_status rb = batch_build(b, psi, w, basis, row_ptr, outcome, count, shots, loss, c_obs, grad_psi,
+                                              grad_w);
+            if (rb) return rb;
+        }
         cudaGraph_t graph = nullptr;
         cudaStream_t cs = b->cap;
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -2711,19 +3181,46 @@ extern "C" qst_status qst_batch_evaluate(qst_batch b, const float *const *psi, c
         }
         qst_status rc = QST_OK;
         const int ns = (int)b->streams.size();
-        if (cudaEventRecord(b->start, cs) != cudaSuccess) rc = QST_ERR_CUDA;
-        for (int j = 0; j < ns && !rc; ++j)
-            if (cudaStreamWaitEvent(b->streams[j], b->start, 0) != cudaSuccess) rc = QST_ERR_CUDA;
-        for (int i = 0; i < b->count && !rc; ++i) {
-            void *si = (void *)b->streams[i % ns];
-            // qst_evaluate: with the instance plan's transform cache (two-round plans) the
-            // adjoint applies only the inverse rounds
-            rc = qst_evaluate(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i], nullptr,
-                              c_obs[i], loss[i], grad_psi[i], grad_w[i], si);
+        if (!b->multi) {
+            if (cudaEventRecord(b->start, cs) != cudaSuccess) rc = QST_ERR_CUDA;
+            for (int j = 0; j < ns && !rc; ++j)
+                if (cudaStreamWaitEvent(b->streams[j], b->start, 0) != cudaSuccess) rc = QST_ERR_CUDA;
         }
-        for (int j = 0; j < ns && !rc; ++j)
-            if (cudaEventRecord(b->join[j], b->streams[j]) != cudaSuccess || cudaStreamWaitEvent(cs, b->join[j], 0) != cudaSuccess)
-                rc = QST_ERR_CUDA;
+        if (b->multi) {
+            // one launch per phase and kernel family; a phase's families run on forked streams
+            for (int ph = 0; ph < kPhases && !rc; ++ph) {
+                std::vector<const BatchLaunch *> L;
+                for (const auto &l : b->launches)
+                    if (l.phase == ph) L.push_back(&l);
+                if (L.size() == 1) {
+                    batch_launch(b, *L[0], cs);
+                    continue;
+                }
+                if (L.empty()) continue;
+                if (cudaEventRecord(b->start, cs) != cudaSuccess) rc = QST_ERR_CUDA;
+                const int used = (int)L.size() < ns ? (int)L.size() : ns;
+                for (int j = 0; j < used && !rc; ++j)
+                    if (cudaStreamWaitEvent(b->streams[j], b->start, 0) != cudaSuccess) rc = QST_ERR_CUDA;
+                for (size_t j = 0; j < L.size() && !rc; ++j) batch_launch(b, *L[j], b->streams[j % ns]);
+                for (int j = 0; j < used && !rc; ++j)
+                    if (cudaEventRecord(b->join[j], b->streams[j]) != cudaSuccess ||
+                        cudaStreamWaitEvent(cs, b->join[j], 0) != cudaSuccess)
+                        rc = QST_ERR_CUDA;
+            }
+            if (!rc && cudaGetLastError() != cudaSuccess) rc = QST_ERR_CUDA;
+        } else {
+            for (int i = 0; i < b->count && !rc; ++i) {
+                void *si = (void *)b->streams[i % ns];
+                // qst_evaluate: with the instance plan's transform cache (two-round plans) the
+                // adjoint applies only the inverse rounds
+                rc = qst_evaluate(b->plans[i], psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i],
+                                  nullptr, c_obs[i], loss[i], grad_psi[i], grad_w[i], si);
+            }
+            for (int j = 0; j < ns && !rc; ++j)
+                if (cudaEventRecord(b->join[j], b->streams[j]) != cudaSuccess ||
+                    cudaStreamWaitEvent(cs, b->join[j], 0) != cudaSuccess)
+                    rc = QST_ERR_CUDA;
+        }
         const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
         if (rc || ec != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);

@@ -197,7 +197,7 @@ __device__ __forceinline__ void fx_exchange(float2 (&v)[16], float2 *work, int f
 }
 
 // Forward unit = (bin, high pattern f, atom k), as k_forward, with fixed rounds.
-__global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
+__device__ __forceinline__ void forward_fx_body(const FwdArgs a, const int cta) {
     constexpr FxSmem sp = fx_smem(false);
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *work = reinterpret_cast<float2 *>(smem + sp.work);
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int k = unit % a.K;
     const int rest = unit / a.K;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
         }
         const float sc = wk * mt.cs;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) pbuf[b2 + fx_roff<2>(i)] = sc * (v[i].x * v[i].x + v[i].y * v[i].y);
+        for (int i = 0; i < 16; ++i) pbuf[b2 + fx_roff<2>(i)] = scaled_abs2(sc, v[i]);
         cp_async_wait1();
         __syncthreads();
         const uint32_t *st = stage + (si & 1) * kFxStage;
@@ -288,11 +288,19 @@ __global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
         tm_dealloc(tmem_sm[0], kFxColsFwd);
     }
 }
+__global__ void __launch_bounds__(kFxT, 3) k_forward_fx(const FwdArgs a) {
+    forward_fx_body(a, blockIdx.x);
+}
+__global__ void __launch_bounds__(kFxT, 3) k_forward_fx_multi(const FwdArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const FwdArgs a = args[i];
+    forward_fx_body(a, (int)blockIdx.x - start[i]);
+}
 
 // Adjoint unit = (bin, high pattern f, atom k), as k_adjoint, with fixed
 // rounds: forward rounds 0, 1, 2, the c multiply in round 2's layout, inverse
 // rounds 2, 1, 0 and the accumulator z (TMEM) in round 0's layout.
-__global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx(const AdjArgs a) {
+__device__ __forceinline__ void adjoint_fx_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
     constexpr FxSmem sp = fx_smem(true);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx(const AdjArgs a) {
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int k = unit % a.K;
     const int rest = unit / a.K;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -386,8 +394,8 @@ __global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx(const AdjArgs a) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const float cc = cden[b2 + fx_roff<2>(i)];
-            v[i].x *= cc;
-            v[i].y *= cc;
+            v[i].x = __fmul_rn(v[i].x, cc);  // not contracted into the butterflies that follow
+            v[i].y = __fmul_rn(v[i].y, cc);
         }
         // inverse rounds 2, 1, 0 (the block barrier of 1 -> 0 also ends every read of the c buffer)
 #pragma unroll
@@ -426,4 +434,12 @@ __global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx(const AdjArgs a) {
         tm_fence_after();
         tm_dealloc(tmem_sm[0], kFxColsAdj);
     }
+}
+__global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx(const AdjArgs a) {
+    adjoint_fx_body(a, blockIdx.x);
+}
+__global__ void __launch_bounds__(kFxT, 3) k_adjoint_fx_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const AdjArgs a = args[i];
+    adjoint_fx_body(a, (int)blockIdx.x - start[i]);
 }

@@ -215,7 +215,7 @@ __device__ __forceinline__ void k2_load_B(float2 (&v)[64], const float2 *wk, uin
 // it read), and the gather also stores them, unscaled, at the observed
 // outcomes into the atom's slice of a.phi_obs, for the cached adjoint.
 template <bool CACHE>
-__global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
+__device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) {
     constexpr K2Smem sp = k2_smem_fwd();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem + sp.stage);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
     const int KP = (a.K + 1) >> 1;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int kp = unit % KP;
     const int rest = unit / KP;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -286,10 +286,10 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 float4 o;
-                o.x = sc * (v[4 * q].x * v[4 * q].x + v[4 * q].y * v[4 * q].y);
-                o.y = sc * (v[4 * q + 1].x * v[4 * q + 1].x + v[4 * q + 1].y * v[4 * q + 1].y);
-                o.z = sc * (v[4 * q + 2].x * v[4 * q + 2].x + v[4 * q + 2].y * v[4 * q + 2].y);
-                o.w = sc * (v[4 * q + 3].x * v[4 * q + 3].x + v[4 * q + 3].y * v[4 * q + 3].y);
+                o.x = scaled_abs2(sc, v[4 * q]);
+                o.y = scaled_abs2(sc, v[4 * q + 1]);
+                o.z = scaled_abs2(sc, v[4 * q + 2]);
+                o.w = scaled_abs2(sc, v[4 * q + 3]);
                 p4[q] = o;
             }
         }
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
             for (int j = t; j < mt.cnt; j += 64) {
                 const uint32_t u = (j < k2Stage ? st[j] : outcome[mt.lo + j]) & cmask;
                 const float2 ph = wk[k2Row * (u >> 6) + (u & 63u)];
-                pk[mt.lo + j] = sc * (ph.x * ph.x + ph.y * ph.y);
+                pk[mt.lo + j] = scaled_abs2(sc, ph);
                 phk[mt.lo + j] = ph;
             }
             if (a.p_dense) {
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
                 float *pd = a.p_dense + (size_t)s * D + ((size_t)f << 12);
                 for (uint32_t u = t; u <= cmask; u += 64) {
                     const float2 ph = wk[k2Row * (u >> 6) + (u & 63u)];
-                    atomicAdd(pd + u, sc * (ph.x * ph.x + ph.y * ph.y));
+                    atomicAdd(pd + u, scaled_abs2(sc, ph));
                 }
             }
         } else if (active) {
@@ -335,5 +335,15 @@ __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
         tm_fence_after();
         tm_dealloc(tmem_sm[0], k2ColsFwd);
     }
+}
+template <bool CACHE>
+__global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
+    forward_2r_body<CACHE>(a, blockIdx.x);
+}
+template <bool CACHE>
+__global__ void __launch_bounds__(k2T, 3) k_forward_2r_multi(const FwdArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const FwdArgs a = args[i];
+    forward_2r_body<CACHE>(a, (int)blockIdx.x - start[i]);
 }
 

@@ -413,7 +413,7 @@ __device__ __forceinline__ void k2p_load_B(f2p (&X)[32], f2p (&Y)[32], const flo
 //     first barrier, and which setting si + 1 reads after its first barrier.
 // A thread's round-A (round-B) exchange addresses are the same in both
 // directions, so it only overwrites addresses that it has read itself.
-__global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
+__device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
     constexpr K2Smem sp = k2p_smem();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
     const int KP = (a.K + 1) >> 1;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int kp = unit % KP;
     const int rest = unit / KP;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -548,6 +548,14 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
         tm_dealloc(tmem_sm[0], k2ColsAdj);
     }
 }
+__global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
+    adjoint_2r_body(a, blockIdx.x);
+}
+__global__ void __launch_bounds__(k2T, 2) k_adjoint_2r_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const AdjArgs a = args[i];
+    adjoint_2r_body(a, (int)blockIdx.x - start[i]);
+}
 
 // Cached adjoint (the evaluate path): the forward kernel has stored the chunk
 // transform phi = K_s psi_k of every setting at its observed outcomes (K_s the
@@ -606,7 +614,7 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-__global__ void __launch_bounds__(k2T, 2) k_adjoint_2c(const AdjArgs a) {
+__device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
     constexpr K2cSmem sp = k2c_smem();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -615,7 +623,7 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2c(const AdjArgs a) {
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
     const int KP = (a.K + 1) >> 1;
-    const int unit = blockIdx.x;
+    const int unit = cta;
     const int kp = unit % KP;
     const int rest = unit / KP;
     const uint32_t f = rest & ((1u << a.r) - 1u);
@@ -724,4 +732,12 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2c(const AdjArgs a) {
         tm_fence_after();
         tm_dealloc(tmem_sm[0], k2cCols);
     }
+}
+__global__ void __launch_bounds__(k2T, 2) k_adjoint_2c(const AdjArgs a) {
+    adjoint_2c_body(a, blockIdx.x);
+}
+__global__ void __launch_bounds__(k2T, 2) k_adjoint_2c_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
+    const int i = multi_find(start, count, (int)blockIdx.x);
+    const AdjArgs a = args[i];
+    adjoint_2c_body(a, (int)blockIdx.x - start[i]);
 }
