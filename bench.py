@@ -66,7 +66,7 @@ def parse_args():
                     help="chunk transforms of two-round plans: 0 FP32 butterflies; 1..3 tensor-core products "
                          "over 6-qubit groups with the data split into that many BF16 terms (the line then also "
                          "times the FP32 plan on the same data: field vs_fp32)")
-    ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2],
+    ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="12-qubit chunk kernels: 2 = two 6-qubit rounds, 1 = three 4-qubit rounds, "
                          "0 = rounds chosen per setting, -1 = the plan's automatic choice")
     return ap.parse_args()
@@ -256,8 +256,8 @@ def batched_eval(flush, reps=10):
     return {"workload": "64 instances, synth.make_batch(seed=0)", "amplitudes_per_eval": int(amps),
             "ms_per_eval": t_graph, "value": amps / t_graph * 1e3, "unit": "amplitudes/s",
             "sequential_ms_per_eval": t_seq, "sequential_value": amps / t_seq * 1e3,
-            "how": "qst.Batch: every instance's forward + adjoint in one captured CUDA graph (forked streams); "
-                   "sequential: one plan per instance, called in order"}
+            "how": "qst.Batch: one launch per phase and kernel family over all instances' CTAs, captured in one "
+                   "CUDA graph; sequential: one plan per instance, called in order"}
 
 
 def run_reference(args):

@@ -62,13 +62,17 @@ typedef struct qst_params {
     int max_bin_settings; /* cap on settings per work bin; 0 = auto */
     int validate;         /* 1 = check basis and CSR on the device (default 1) */
     int reg_bits;         /* amplitudes per thread per round = 2^reg_bits: 4 or 5; 0 = auto */
-    int fixed_rounds;     /* 12-qubit chunks only.  2 = two rounds of six qubits, 64 amplitudes per
-                             thread, two atoms per CTA (one shared-memory exchange per setting in
-                             the forward, two in the adjoint; n <= 16 only, n = 17..20 runs 1);
-                             1 = three rounds of four qubits on fixed qubit groups, 16 amplitudes
-                             per thread (compile-time shared-memory offsets, warp-local middle
-                             exchange); 0 = rounds chosen per setting; -1 = automatic: 2 when a
-                             work bin may hold >= 32 settings, else 1.  Other values:
+    int fixed_rounds;     /* chunk kernels.  12-qubit chunks: 2 = two rounds of six qubits, 64
+                             amplitudes per thread, two atoms per CTA (one shared-memory exchange per
+                             setting in the forward, two in the adjoint; n <= 16 only, n = 17..20
+                             runs 1); 1 = three rounds of four qubits on fixed qubit groups, 16
+                             amplitudes per thread (compile-time shared-memory offsets, warp-local
+                             middle exchange).  States of 5..9 qubits held in one chunk: 3 = one
+                             warp per (bin, atom), 2^(n-5) amplitudes per lane, the low five bits'
+                             butterflies by lane shuffles (QST_ERR_UNSUPPORTED for other plans).
+                             0 = rounds chosen per setting (one CTA per (bin, atom)); -1 =
+                             automatic: 3 for whole states of 5..9 qubits, for 12-qubit chunks 2
+                             when a work bin may hold >= 32 settings, else 1.  Other values:
                              QST_ERR_INVALID_ARG.  Default -1. */
     int phi_cache;        /* qst_evaluate's transform cache: the forward stores the transform of every
                              atom at every observed outcome (K x nnz complex64, owned by the plan) and
@@ -119,8 +123,9 @@ qst_status qst_plan_workspace_bytes(qst_plan plan, int64_t *bytes);
 
 /* The plan's chunk geometry: qubits transformed on-chip per work unit, high
  * qubits applied outside the chunk (by setting bins, or by butterfly passes
- * for n = 17..20), and which chunk kernels run: 2 = two 6-qubit rounds,
- * 1 = three fixed 4-qubit rounds, 0 = rounds chosen per setting.  Any output
+ * for n = 17..20), and which chunk kernels run: 3 = a warp per (bin, atom),
+ * 2 = two 6-qubit rounds, 1 = three fixed 4-qubit rounds, 0 = rounds chosen
+ * per setting.  Any output
  * pointer may be NULL.  Host only. */
 qst_status qst_plan_geometry(qst_plan plan, int *chunk_qubits, int *high_qubits, int *fixed_rounds);
 
@@ -370,9 +375,9 @@ qst_status qst_iterate_state(qst_plan plan, int *stopped, long long *oracle_call
  * Batched evaluation of many independent instances of uneven shape
  * (instances with different n, M, K and shots, e.g. 64 instances with n from
  * 6 to 14).  qst_batch_create makes one plan per instance (params shared;
- * unless params fixes max_bin_settings, every plan bins up to 96 settings,
- * because the instances fill the GPU together: 12-qubit chunks then run the
- * two-round kernels).  qst_batch_evaluate runs every instance's qst_evaluate
+ * unless params fixes max_bin_settings, plans of n = 12..16 bin up to 96
+ * settings, because the instances fill the GPU together: their 12-qubit
+ * chunks then run the two-round kernels).  qst_batch_evaluate runs every instance's qst_evaluate
  * (forward, then the adjoint with the instance plan's transform cache where
  * it has one); arguments are HOST arrays of `count` DEVICE pointers, one per
  * instance, with the per-instance layouts of qst_forward / qst_adjoint

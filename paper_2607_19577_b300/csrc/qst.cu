@@ -1086,6 +1086,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_fixed.cuh"
 #include "qst_tworound.cuh"
 #include "qst_tworound_packed.cuh"
+#include "qst_warp.cuh"
 #include "qst_tensorcore.cuh"
 #include "qst_single.cuh"
 #include "qst_iterate.cuh"
@@ -1110,6 +1111,7 @@ struct qst_plan_s {
     bool wide = false;       // n = 17..20: high bits by butterfly passes, groups of wide_G settings
     bool fx = false;         // 12-qubit chunks with fixed-position rounds (k_forward_fx / k_adjoint_fx)
     bool fx2 = false;        // 12-qubit chunks in two 6-bit rounds, two atoms per CTA (k_forward_2r / k_adjoint_2r)
+    bool fw = false;         // states of 5..9 qubits in one chunk: a warp per (bin, atom) (k_forward_wu / k_adjoint_wu)
     float2 *phi = nullptr;   // [K][nnz] transform cache of qst_evaluate (two-round plans, params.phi_cache)
     bool cache_on = false;   // qst_evaluate passes phi from the forward to the adjoint
     unsigned char *tc_ops = nullptr;  // precision > 0: the 729 six-qubit group operators (B operand layout)
@@ -1283,6 +1285,14 @@ void launch_forward_units(qst_plan p, const FwdArgs &a0, int units, cudaStream_t
         else launch_forward_tc<3>(a, grid, st);
         return;
     }
+    if (p->fw) {
+        const int grid = (int)(((int64_t)units * p->K + kWuT / 32 - 1) / (kWuT / 32));
+        with_wu(p->n, [&](auto nb) {
+            constexpr int NB = decltype(nb)::value;
+            k_forward_wu<NB><<<grid, kWuT, wu_smem(NB), st>>>(a);
+        });
+        return;
+    }
     if (p->fx2) {
         if (a.phi_obs) k_forward_2r<true><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
         else k_forward_2r<false><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
@@ -1312,6 +1322,14 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
         if (p->prm.precision == 1) k_adjoint_tc<1><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
         else if (p->prm.precision == 2) k_adjoint_tc<2><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
         else k_adjoint_tc<3><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
+        return;
+    }
+    if (p->fw) {
+        const int grid = (int)(((int64_t)units * p->K + kWuT / 32 - 1) / (kWuT / 32));
+        with_wu(p->n, [&](auto nb) {
+            constexpr int NB = decltype(nb)::value;
+            k_adjoint_wu<NB><<<grid, kWuT, wu_smem(NB), st>>>(a);
+        });
         return;
     }
     if (p->fx2 && a.phi_obs) {
@@ -1523,7 +1541,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
-    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 2 || prm.phi_cache < -1 || prm.phi_cache > 1 ||
+    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 3 || prm.phi_cache < -1 || prm.phi_cache > 1 ||
         prm.precision < 0 || prm.precision > 3) {
         delete p;
         return QST_ERR_INVALID_ARG;
@@ -1550,6 +1568,14 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (p->smax >= 32 ? 2 : 1);
     p->fx2 = c == 12 && fr == 2 && !wide;
     p->fx = c == 12 && p->A == 4 && (fr == 1 || (fr == 2 && wide));
+    // whole states of 5..9 qubits: warp-per-unit kernels unless per-setting rounds are asked for
+    // (0); from 10 qubits on a lane's 32 amplitudes and accumulator need ~250 registers and the
+    // CTA kernels measured faster (3.3 against 1.8 ms on the batched workload's n = 10 instances)
+    p->fw = !wide && r == 0 && c >= 5 && c <= kWuMaxQubits && (prm.fixed_rounds == -1 || prm.fixed_rounds == 3);
+    if (prm.fixed_rounds == 3 && !p->fw) {
+        delete p;
+        return QST_ERR_UNSUPPORTED;
+    }
     // the cached adjoint exists for the two-round kernels and the wide path's single-setting
     // 12-qubit-chunk kernels (n = 20)
     if (prm.phi_cache == 1 && !p->fx2 && !(wide && p->fx)) {
@@ -1747,7 +1773,7 @@ qst_status qst_plan_geometry(qst_plan p, int *chunk_qubits, int *high_qubits, in
     if (!p) return QST_ERR_INVALID_ARG;
     if (chunk_qubits) *chunk_qubits = p->c;
     if (high_qubits) *high_qubits = p->r;
-    if (fixed_rounds) *fixed_rounds = p->fx2 ? 2 : (p->fx ? 1 : 0);
+    if (fixed_rounds) *fixed_rounds = p->fw ? 3 : (p->fx2 ? 2 : (p->fx ? 1 : 0));
     return QST_OK;
 }
 
@@ -2789,8 +2815,10 @@ __global__ void __launch_bounds__(256) k_hsum_multi(const HsumArgs *__restrict__
 
 // Chunk-kernel family of a plan: the multi-instance forward / adjoint
 // launches group instances by it (same kernel, block and shared memory).
-enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3 };  // >= 0: generic kernels, 100 c + A
+// >= 0: generic kernels, 100 c + A; -10 - n: warp-unit kernels of n qubits
+enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3 };
 int plan_family(const qst_plan_s *p) {
+    if (p->fw) return -10 - p->n;
     if (p->fx2) return p->cache_on ? kFam2rCache : kFam2r;
     if (p->fx) return kFamFx;
     return 100 * p->c + p->A;
@@ -2798,6 +2826,7 @@ int plan_family(const qst_plan_s *p) {
 // CTAs of one instance's forward / adjoint grid
 int64_t plan_unit_ctas(const qst_plan_s *p) {
     const int64_t units = (int64_t)p->nb_max << p->r;
+    if (p->fw) return (units * p->K + kWuT / 32 - 1) / (kWuT / 32);
     return units * (p->fx2 ? (p->K + 1) / 2 : p->K);
 }
 
@@ -2853,6 +2882,8 @@ void set_family_attrs(int fam) {
         cudaFuncSetAttribute(k_forward_2r_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_adjoint_2c_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem().total);
         cudaFuncSetAttribute(k_adjoint_2r_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+    } else if (fam <= -15) {
+        // at most 16 KB of shared memory: no attribute
     } else if (fam == kFamFx) {
         cudaFuncSetAttribute(k_forward_fx_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(false).total);
         cudaFuncSetAttribute(k_adjoint_fx_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
@@ -2876,14 +2907,18 @@ extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, 
     if (!b) return QST_ERR_NO_MEMORY;
     b->count = count;
     b->plans.assign(count, nullptr);
-    // The instances share the GPU, so no plan needs small bins to fill it alone:
-    // unless the caller fixes max_bin_settings, every plan bins up to kMaxBin
-    // settings (12-qubit chunks then run the two-round kernels).
-    qst_params prm;
-    qst_params_default(&prm);
-    if (params) prm = *params;
-    if (!params || params->max_bin_settings == 0) prm.max_bin_settings = kMaxBin;
+    // The instances share the GPU, so a plan of 12-qubit chunks needs no small
+    // bins to fill it alone: unless the caller fixes max_bin_settings, plans of
+    // n = 12..16 bin up to kMaxBin settings (and run the two-round kernels).
+    // Smaller states keep their own bin sizes: their units are a warp or a small
+    // CTA per (bin, atom), and many short bins keep the SMs busy.
+    qst_params prm0;
+    qst_params_default(&prm0);
+    if (params) prm0 = *params;
     for (int i = 0; i < count; ++i) {
+        qst_params prm = prm0;
+        if (prm0.max_bin_settings == 0 && n[i] >= kMaxChunk && n[i] <= kMaxChunk + kMaxTop)
+            prm.max_bin_settings = kMaxBin;
         const qst_status rc = qst_plan_create(&b->plans[i], n[i], M[i], K[i], nnz[i], &prm);
         if (rc) {
             qst_batch_destroy(b);
@@ -3121,6 +3156,11 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
             if (fam == kFam2rCache) k_forward_2r_multi<true><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFam2r) k_forward_2r_multi<false><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_forward_fx_multi<<<grid, kFxT, fx_smem(false).total, st>>>(a, start, cnt);
+            else if (fam <= -15)
+                with_wu(-10 - fam, [&](auto nb) {
+                    constexpr int NB = decltype(nb)::value;
+                    k_forward_wu_multi<NB><<<grid, kWuT, wu_smem(NB), st>>>(a, start, cnt);
+                });
             else
                 with_geo(fam / 100, fam % 100, [&](auto cc, auto ra) {
                     constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;
@@ -3133,6 +3173,11 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
             if (fam == kFam2rCache) k_adjoint_2c_multi<<<grid, k2T, k2c_smem().total, st>>>(a, start, cnt);
             else if (fam == kFam2r) k_adjoint_2r_multi<<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_adjoint_fx_multi<<<grid, kFxT, fx_smem(true).total, st>>>(a, start, cnt);
+            else if (fam <= -15)
+                with_wu(-10 - fam, [&](auto nb) {
+                    constexpr int NB = decltype(nb)::value;
+                    k_adjoint_wu_multi<NB><<<grid, kWuT, wu_smem(NB), st>>>(a, start, cnt);
+                });
             else
                 with_geo(fam / 100, fam % 100, [&](auto cc, auto ra) {
                     constexpr int C = decltype(cc)::value, RA = decltype(ra)::value;

@@ -168,8 +168,9 @@ class Plan:
         lib.qst_params_default(ctypes.byref(prm))
         prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
         prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
-        # fixed_rounds (12-qubit chunks): 2 = two 6-qubit rounds, 1 = three 4-qubit
-        # rounds, 0 = per-setting rounds, -1 = automatic (True / False mean 1 / 0)
+        # fixed_rounds: 12-qubit chunks 2 = two 6-qubit rounds, 1 = three 4-qubit rounds;
+        # whole states of 5..9 qubits 3 = a warp per (bin, atom); 0 = per-setting rounds,
+        # -1 = automatic (True / False mean 1 / 0)
         prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(fixed_rounds)
         # phi_cache: qst_evaluate's transform cache (two-round plans): 1 on, 0 off, -1 automatic
         prm.phi_cache = int(phi_cache)
@@ -212,7 +213,7 @@ class Plan:
         return out
 
     def geometry(self):
-        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan (fixed_rounds:
+        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan (fixed_rounds: 3 = warp units,
         2 = two 6-qubit rounds, 1 = three 4-qubit rounds, 0 = per-setting rounds)."""
         c, r, fx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().qst_plan_geometry(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(fx)), "geometry")
@@ -550,7 +551,8 @@ def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
     (CUDA events on the current stream) over candidate (reg_bits, chunk_qubits,
     max_bin_settings, fixed_rounds) choices: 16 or 32 amplitudes per thread and
     round, the default chunk or one bit smaller, automatic or fixed bin sizes,
-    and two 6-qubit, three 4-qubit or per-setting rounds.
+    and two 6-qubit, three 4-qubit or per-setting rounds (states of 5..10
+    qubits up to 9: a warp per unit or per-setting rounds).
 
     Returns (best params dict, [(params, ms per evaluation), ...])."""
     K, D = psi.shape
@@ -559,8 +561,9 @@ def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
     if candidates is None:
         c0 = n if n <= 12 else (12 if n <= 16 else n - 8)
         chunks = [0] + ([c0 - 1] if 13 <= n <= 16 and c0 - 1 >= n - 4 else [])
+        fxs = (3, 0) if 5 <= n <= 9 else (2, 1, 0)
         candidates = [dict(reg_bits=rb, chunk_qubits=c, max_bin_settings=sm, fixed_rounds=fx)
-                      for rb in (4, 5) for c in chunks for sm in (0, 32) for fx in (2, 1, 0)
+                      for rb in (4, 5) for c in chunks for sm in (0, 32) for fx in fxs
                       if not (fx and rb == 5)]
     results = []
     for prm in candidates:

@@ -365,3 +365,21 @@ def test_evaluate_without_cache_and_other_families():
             assert np.array_equal(ev[key], sep[key]), (kw, key)
     with pytest.raises(qst.QSTError):
         qst.Plan(inst.n, inst.M, inst.K, inst.nnz, fixed_rounds=1, phi_cache=1)
+
+
+@pytest.mark.parametrize("n,M,K,smax,seed", [(5, 20, 3, 0, 0), (6, 37, 2, 5, 1), (8, 64, 5, 0, 2), (9, 30, 4, 96, 3),
+                                              (9, 41, 3, 1, 4)])
+def test_warp_unit_kernels(n, M, K, smax, seed):
+    """States of 5..9 qubits in one chunk: a warp per (bin, atom), butterflies on
+    the low five bits by lane shuffles (fixed_rounds = 3, the automatic choice)
+    and the per-setting-round CTA kernels (fixed_rounds = 0), both against the
+    oracle, dense p included; odd K, single-setting and full bins."""
+    inst = synth.random_instance(n, M, K, 40 << min(n, 8), 1700 + seed)
+    ref = run_oracle(inst, dense=True)
+    for fr in (3, 0):
+        compare(inst, run_gpu(inst, dense=True, fixed_rounds=fr, max_bin_settings=smax), ref, dense=True)
+    plan = qst.Plan(n, M, K, inst.nnz)
+    assert plan.geometry()["fixed_rounds"] == 3
+    plan.close()
+    with pytest.raises(qst.QSTError):
+        qst.Plan(10, M, K, inst.nnz, fixed_rounds=3)
