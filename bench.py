@@ -206,7 +206,7 @@ def cpu_oracle_rate_all_cores(inst, budget_s, rate_1core, threads):
     return S, time.perf_counter() - t0
 
 
-def batched_eval(flush, reps=10):
+def batched_eval(flush, reps=10, autotune=False):
     """The batched workload (64 independent instances, n uniform in 6..14, rank
     1..8, K = 2 rank, 200..3000 settings, 500..5000 shots; synth.make_batch(seed=0)):
     one forward + adjoint of every instance per evaluation, through qst.Batch (one
@@ -253,11 +253,23 @@ def batched_eval(flush, reps=10):
     for p in plans:
         p.close()
     batch.close()
-    return {"workload": "64 instances, synth.make_batch(seed=0)", "amplitudes_per_eval": int(amps),
-            "ms_per_eval": t_graph, "value": amps / t_graph * 1e3, "unit": "amplitudes/s",
-            "sequential_ms_per_eval": t_seq, "sequential_value": amps / t_seq * 1e3,
-            "how": "qst.Batch: one launch per phase and kernel family over all instances' CTAs, captured in one "
-                   "CUDA graph; sequential: one plan per instance, called in order"}
+    out = {"workload": "64 instances, synth.make_batch(seed=0)", "amplitudes_per_eval": int(amps),
+           "ms_per_eval": t_graph, "value": amps / t_graph * 1e3, "unit": "amplitudes/s",
+           "sequential_ms_per_eval": t_seq, "sequential_value": amps / t_seq * 1e3,
+           "how": "qst.Batch: one launch per phase and kernel family over all instances' CTAs, captured in one "
+                  "CUDA graph; sequential: one plan per instance, called in order"}
+    if autotune:
+        shapes = [(i.n, i.M, i.K, i.nnz) for i in insts]
+        chosen, table = qst.autotune_batch(shapes, psis, ws_, datas)
+        batch = qst.Batch(shapes, params=chosen)
+        t_tuned = timed(graph)
+        batch.close()
+        out["autotuned"] = {"ms_per_eval": t_tuned, "value": amps / t_tuned * 1e3,
+                            "choice_per_n": {str(i.n): c for i, c in zip(insts, chosen)},
+                            "table": [{"n": n, "params": c, "ms": ms} for n, c, ms in table],
+                            "how": "qst.autotune_batch: per size class, the class's instances timed as one batch "
+                                   "under each candidate layout; the fastest per class"}
+    return out
 
 
 def run_reference(args):
@@ -610,7 +622,7 @@ def run_ours(args):
 
     batched = None
     if ws == 1 and not args.no_batched and not args.shard:
-        batched = batched_eval(flush)
+        batched = batched_eval(flush, autotune=args.autotune)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

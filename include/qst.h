@@ -375,7 +375,7 @@ qst_status qst_iterate_state(qst_plan plan, int *stopped, long long *oracle_call
  * Batched evaluation of many independent instances of uneven shape
  * (instances with different n, M, K and shots, e.g. 64 instances with n from
  * 6 to 14).  qst_batch_create makes one plan per instance (params shared;
- * unless params fixes max_bin_settings, plans of n = 12..16 bin up to 96
+ * unless params fixes max_bin_settings, plans of n = 10..16 bin up to 32
  * settings, because the instances fill the GPU together: their 12-qubit
  * chunks then run the two-round kernels).  qst_batch_evaluate runs every instance's qst_evaluate
  * (forward, then the adjoint with the instance plan's transform cache where
@@ -397,6 +397,11 @@ qst_status qst_iterate_state(qst_plan plan, int *stopped, long long *oracle_call
 typedef struct qst_batch_s *qst_batch;
 qst_status qst_batch_create(qst_batch *batch, int count, const int *n, const int *M,
                             const int *K, const int64_t *nnz, const qst_params *params);
+/* The same with one params record per instance (params[0..count-1], taken as
+ * given: no batch-wide bin rule), e.g. the layouts an autotuner chose per
+ * size class.  params == NULL: QST_ERR_INVALID_ARG. */
+qst_status qst_batch_create_each(qst_batch *batch, int count, const int *n, const int *M,
+                                 const int *K, const int64_t *nnz, const qst_params *params);
 qst_status qst_batch_destroy(qst_batch batch);
 qst_status qst_batch_plan(qst_batch batch, int i, qst_plan *plan);
 qst_status qst_batch_evaluate(qst_batch batch, const float *const *psi, const float *const *w,

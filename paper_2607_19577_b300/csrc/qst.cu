@@ -2831,6 +2831,7 @@ int64_t plan_unit_ctas(const qst_plan_s *p) {
 }
 
 constexpr int kBatchStreams = 16;
+constexpr int kBatchBin = 32;  // settings per bin of a batch plan of 10..16 qubits (see batch_create)
 
 enum BatchPhase { kPhPack, kPhValidate, kPhForward, kPhEpilogue, kPhLoss, kPhAdjoint, kPhReduce, kPhHsum, kPhases };
 
@@ -2899,26 +2900,30 @@ void set_family_attrs(int fam) {
 }
 }  // namespace
 
-extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, const int *M, const int *K,
-                                       const int64_t *nnz, const qst_params *params) {
-    if (!out || count < 1 || !n || !M || !K || !nnz) return QST_ERR_INVALID_ARG;
+namespace {
+// params: one record for all instances (each == false; the batch bin rule
+// below applies) or one per instance (each == true; taken as given).
+qst_status batch_create(qst_batch *out, int count, const int *n, const int *M, const int *K, const int64_t *nnz,
+                        const qst_params *params, bool each) {
+    if (!out || count < 1 || !n || !M || !K || !nnz || (each && !params)) return QST_ERR_INVALID_ARG;
     *out = nullptr;
     qst_batch b = new (std::nothrow) qst_batch_s;
     if (!b) return QST_ERR_NO_MEMORY;
     b->count = count;
     b->plans.assign(count, nullptr);
-    // The instances share the GPU, so a plan of 12-qubit chunks needs no small
-    // bins to fill it alone: unless the caller fixes max_bin_settings, plans of
-    // n = 12..16 bin up to kMaxBin settings (and run the two-round kernels).
-    // Smaller states keep their own bin sizes: their units are a warp or a small
-    // CTA per (bin, atom), and many short bins keep the SMs busy.
+    // The instances share the GPU, so a plan of 10..16 qubits needs no small bins
+    // to fill it alone: unless the caller fixes max_bin_settings, such plans bin
+    // up to kBatchBin settings (12-qubit chunks then run the two-round kernels).
+    // The batch autotuner picked these bins for every class of n >= 10 on the
+    // 64-instance workload.  Smaller states keep their own bin sizes: their units
+    // are a warp per (bin, atom), and many short bins keep the SMs busy.
     qst_params prm0;
     qst_params_default(&prm0);
-    if (params) prm0 = *params;
+    if (params && !each) prm0 = *params;
     for (int i = 0; i < count; ++i) {
-        qst_params prm = prm0;
-        if (prm0.max_bin_settings == 0 && n[i] >= kMaxChunk && n[i] <= kMaxChunk + kMaxTop)
-            prm.max_bin_settings = kMaxBin;
+        qst_params prm = each ? params[i] : prm0;
+        if (!each && prm0.max_bin_settings == 0 && n[i] >= 10 && n[i] <= kMaxChunk + kMaxTop)
+            prm.max_bin_settings = kBatchBin;
         const qst_status rc = qst_plan_create(&b->plans[i], n[i], M[i], K[i], nnz[i], &prm);
         if (rc) {
             qst_batch_destroy(b);
@@ -2952,6 +2957,17 @@ extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, 
     }
     *out = b;
     return QST_OK;
+}
+}  // namespace
+
+extern "C" qst_status qst_batch_create(qst_batch *out, int count, const int *n, const int *M, const int *K,
+                                       const int64_t *nnz, const qst_params *params) {
+    return batch_create(out, count, n, M, K, nnz, params, false);
+}
+
+extern "C" qst_status qst_batch_create_each(qst_batch *out, int count, const int *n, const int *M, const int *K,
+                                            const int64_t *nnz, const qst_params *params) {
+    return batch_create(out, count, n, M, K, nnz, params, true);
 }
 
 extern "C" qst_status qst_batch_plan(qst_batch b, int i, qst_plan *plan) {

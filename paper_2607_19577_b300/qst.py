@@ -92,6 +92,7 @@ def load():
         lib.qst_simplex_project.argtypes = [P, i32, f64, P, P, P, P]
         lib.qst_refactor.argtypes = [P, P, P, f64, P, P]
         lib.qst_batch_create.argtypes = [ctypes.POINTER(P), i32, P, P, P, P, ctypes.POINTER(_Params)]
+        lib.qst_batch_create_each.argtypes = [ctypes.POINTER(P), i32, P, P, P, P, ctypes.POINTER(_Params)]
         lib.qst_batch_destroy.argtypes = [P]
         lib.qst_batch_plan.argtypes = [P, i32, ctypes.POINTER(P)]
         lib.qst_batch_evaluate.argtypes = [P] + [P] * 11 + [P]
@@ -103,7 +104,8 @@ def load():
                      "qst_adjoint", "qst_evaluate", "qst_evaluate_host", "qst_plan_status", "qst_plan_set_timing",
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
-                     "qst_batch_create", "qst_batch_destroy", "qst_batch_plan", "qst_batch_evaluate"]:
+                     "qst_batch_create", "qst_batch_create_each", "qst_batch_destroy", "qst_batch_plan",
+                     "qst_batch_evaluate"]:
             getattr(lib, name).restype = i32
         _lib = lib
     return _lib
@@ -493,20 +495,33 @@ def adjoint_noalloc(psi, w, d: Data, c_obs, grad_psi, grad_w, device_status, par
 class Batch:
     """qst_batch: many independent instances evaluated as one captured CUDA graph."""
 
-    def __init__(self, shapes, eps=1e-8, **plan_kw):
-        """shapes: list of (n, M, K, nnz)."""
+    def __init__(self, shapes, eps=1e-8, params=None, **plan_kw):
+        """shapes: list of (n, M, K, nnz).  params: None (plan_kw shared by every
+        instance, with the library's batch bin rule) or one dict of plan parameters
+        per instance (taken as given, e.g. from autotune_batch)."""
         lib = load()
-        prm = _Params()
-        lib.qst_params_default(ctypes.byref(prm))
-        prm.eps = float(eps)
-        for k, v in plan_kw.items():
-            setattr(prm, k, v)
         arr = lambda vals, ct: (ct * len(vals))(*vals)  # noqa: E731
         self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        dims = (arr([s[0] for s in shapes], ctypes.c_int), arr([s[1] for s in shapes], ctypes.c_int),
+                arr([s[2] for s in shapes], ctypes.c_int), arr([s[3] for s in shapes], ctypes.c_int64))
         h = ctypes.c_void_p()
-        _check(lib.qst_batch_create(ctypes.byref(h), len(shapes), arr([s[0] for s in shapes], ctypes.c_int),
-                                    arr([s[1] for s in shapes], ctypes.c_int), arr([s[2] for s in shapes], ctypes.c_int),
-                                    arr([s[3] for s in shapes], ctypes.c_int64), ctypes.byref(prm)), "qst_batch_create")
+        if params is None:
+            prm = _Params()
+            lib.qst_params_default(ctypes.byref(prm))
+            prm.eps = float(eps)
+            for k, v in plan_kw.items():
+                setattr(prm, k, v)
+            _check(lib.qst_batch_create(ctypes.byref(h), len(shapes), *dims, ctypes.byref(prm)), "qst_batch_create")
+        else:
+            if len(params) != len(shapes):
+                raise ValueError("params: one dict per instance")
+            prms = (_Params * len(shapes))()
+            for prm, kw in zip(prms, params):
+                lib.qst_params_default(ctypes.byref(prm))
+                prm.eps = float(eps)
+                for k, v in {**plan_kw, **kw}.items():
+                    setattr(prm, k, v)
+            _check(lib.qst_batch_create_each(ctypes.byref(h), len(shapes), *dims, prms), "qst_batch_create_each")
         self._h = h
 
     def close(self):
@@ -587,3 +602,55 @@ def autotune(psi, w, d: Data, eps=1e-8, candidates=None, warmup=2, reps=3):
         plan.close()
     results.sort(key=lambda x: x[1])
     return results[0][0], results
+
+
+def batch_candidates(n):
+    """Plan layouts the batch autotuner tries for instances of n qubits."""
+    if 5 <= n <= 9:
+        return ([dict(fixed_rounds=3, max_bin_settings=sm) for sm in (0, 8, 32)] +
+                [dict(fixed_rounds=0, max_bin_settings=sm) for sm in (0, 32)])
+    if 10 <= n <= 11:
+        return [dict(fixed_rounds=0, max_bin_settings=sm, reg_bits=rb) for sm in (0, 32, 96) for rb in (4, 5)]
+    if 12 <= n <= 16:
+        return [dict(fixed_rounds=fr, max_bin_settings=sm) for fr in (2, 1) for sm in (0, 32, 96)]
+    return [dict()]
+
+
+def autotune_batch(shapes, psis, ws, datas, eps=1e-8, warmup=2, reps=3, candidates=batch_candidates):
+    """Pick a plan layout per size class for qst_batch: for the instances of each n,
+    time them as one batch (one launch per phase over the class, as in the full
+    batch, so they share the GPU as they will) under each layout of candidates(n),
+    CUDA events on the current stream, and keep the fastest.  Returns (per-instance
+    params, [(n, params, ms per evaluation), ...])."""
+    classes = {}
+    for i, s in enumerate(shapes):
+        classes.setdefault(int(s[0]), []).append(i)
+    chosen, table = [dict() for _ in shapes], []
+    for n, idx in sorted(classes.items()):
+        best, best_ms = dict(), None
+        ps, w_, ds = [psis[i] for i in idx], [ws[i] for i in idx], [datas[i] for i in idx]
+        losses = [torch.zeros(1, dtype=torch.float64, device=p.device) for p in ps]
+        cs = [torch.zeros(d.nnz, dtype=torch.float32, device=p.device) for p, d in zip(ps, ds)]
+        gs = [torch.zeros_like(p) for p in ps]
+        gws = [torch.zeros_like(x) for x in w_]
+        for cand in candidates(n):
+            try:
+                b = Batch([shapes[i] for i in idx], eps=eps, params=[cand] * len(idx))
+            except QSTError:
+                continue
+            for _ in range(warmup):
+                b.evaluate(ps, w_, ds, losses, cs, gs, gws)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                b.evaluate(ps, w_, ds, losses, cs, gs, gws)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            b.close()
+            table.append((n, cand, ms))
+            if best_ms is None or ms < best_ms:
+                best, best_ms = cand, ms
+        for i in idx:
+            chosen[i] = dict(best)
+    return chosen, table

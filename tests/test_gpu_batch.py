@@ -115,3 +115,30 @@ def test_full_batched_workload_largest_instances_match_oracle():
             assert np.max(np.abs(gg[k] - a["grad_psi"][k])) <= 1e-4 * np.max(np.abs(a["grad_psi"][k])), (j, k)
         np.testing.assert_allclose(gws[j].cpu().numpy(), a["grad_w"], rtol=1e-4)
     b.close()
+
+
+def test_batch_autotuner_per_size_class():
+    """qst.autotune_batch times each size class's instances as one batch under its
+    candidate layouts; the batch built with the chosen per-instance parameters
+    (qst_batch_create_each) agrees with the oracle on every instance."""
+    insts = synth.make_batch(seed=3, count=8, n_range=(6, 12), M_range=(20, 60), shots_range=(100, 400),
+                             rank_range=(1, 3))
+    shapes = [(i.n, i.M, i.K, i.nnz) for i in insts]
+    datas, psis, ws, losses, cs, gs, gws = _alloc(insts)
+    chosen, table = qst.autotune_batch(shapes, psis, ws, datas, warmup=1, reps=1)
+    assert len(chosen) == len(insts) and table
+    for i, c in zip(insts, chosen):
+        assert c in qst.batch_candidates(i.n)
+    b = qst.Batch(shapes, params=chosen)
+    b.evaluate(psis, ws, datas, losses, cs, gs, gws)
+    torch.cuda.synchronize()
+    for j, inst in enumerate(insts):
+        assert b.plan(j).status() == 0
+        psi, w = inst.psi.astype(np.complex128), inst.w.astype(np.float64)
+        f = oracle.forward(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+        a = oracle.adjoint(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, f["c_obs"])
+        assert abs(losses[j].item() - f["loss"]) <= 1e-5 * abs(f["loss"])
+        gg = gs[j].cpu().numpy().astype(np.complex128)
+        for k in range(inst.K):
+            assert np.max(np.abs(gg[k] - a["grad_psi"][k])) <= 1e-4 * np.max(np.abs(a["grad_psi"][k]))
+    b.close()
