@@ -351,8 +351,17 @@ typedef struct qst_iter_params {
                               Sec. III-B over all outcomes for one atom (a response, G v) or one loss /
                               A^T c evaluation, as Algorithm 1 issues them: the starting state costs
                               R + 1; an atom slot 1 + 2 per trial; a coefficient slot 1 + 1 per trial;
-                              a refactor slot (new atoms) + 1.  A trial count is the accepted trial's
-                              index + 1, or the whole grid when none is accepted. */
+                              a refactor slot (new atoms) + 1; a spectral slot, per trial, K per Krylov
+                              block (G on the block), the new atoms + 1.  A trial count is the accepted
+                              trial's index + 1, or the whole grid when none is accepted. */
+    int spectral;          /* T_rho slots: 0 = the exact refactor (qst_refactor, eta_rho = 0) inside the
+                              graph (default); 1 = the spectral step of Sec. III-C (qst_step slot 3): the
+                              iterations between T_rho slots run as graph segments (one graph replayed
+                              for every segment with the same slots) and each T_rho slot runs qst_step
+                              slot 3 on the stream, its J, acceptance and oracle calls entering the same
+                              history and stopping rules; the host synchronises at those slots (the
+                              Krylov block sizes are read there).  Needs what qst_step slot 3 needs
+                              (K <= 16, n <= 16); a run stopped by a rule skips the step. */
 } qst_iter_params;
 void qst_iter_params_default(qst_iter_params *ip);
 qst_status qst_iterate(qst_plan plan, int T, int t0, float *psi, float *w,

@@ -1150,6 +1150,11 @@ struct qst_plan_s {
             *lz_Tc = nullptr;
     double *lz_lam = nullptr;
     int *lz_int = nullptr;  // [0] kept count, [1] selected s
+    int lz_blocks = 0;            // Krylov blocks (adjoint launches) of the last spectral candidate
+    double *it_Jseg = nullptr;    // qst_iterate with spectral slots: a graph segment's J / acceptance history
+    int *it_aseg = nullptr;
+    int it_seg_cap = 0;
+    long long step_calls = 0;     // serial-equivalent oracle calls of the last qst_step slot 3
     // qst_iterate: device state, trial likelihood ratio, captured graph
     IterState *it_state = nullptr;
     float *it_c = nullptr;
@@ -1708,6 +1713,8 @@ qst_status qst_plan_destroy(qst_plan p) {
     if (!p) return QST_ERR_INVALID_ARG;
     cudaFree(p->phi);
     cudaFree(p->tc_ops);
+    cudaFree(p->it_Jseg);
+    cudaFree(p->it_aseg);
     cudaFree(p->plans);
     cudaFree(p->order);
     cudaFree(p->bins);
@@ -2118,12 +2125,14 @@ qst_status spectral_candidate(qst_plan p, const float *psi, const float *w, cons
     if (kb > 0 && cudaMemcpyAsync(p->lz_Q, p->lz_W, vb * kb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return QST_ERR_CUDA;
     m = kb;
+    p->lz_blocks = 0;
     while (kb > 0) {
         // SQ_block = eta G Q_block + Psi diag(w) (Psi^* Q_block); the adjoint takes K rows, zero beyond kb
         float2 *qb = p->lz_Q + (size_t)mb * D, *sq = p->lz_SQ + (size_t)mb * D;
         if (kb < K && cudaMemsetAsync(p->lz_Q + (size_t)m * D, 0, vb * (K - kb), st) != cudaSuccess) return QST_ERR_CUDA;
         rc = adjoint_core(p, reinterpret_cast<const float *>(qb), p->step_m1, row_ptr, outcome, p->step_c,
                           reinterpret_cast<float *>(sq), nullptr, st);
+        p->lz_blocks += 1;
         if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
             k_xgram<<<K * kb, 256, 0, st>>>(ps, K, qb, kb, D, p->lz_C, kb);
         });
@@ -2204,6 +2213,7 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
     const size_t D = (size_t)1 << p->n;
     std::vector<float> wh((size_t)K);
     // J = L_eps + mu R for the state (ps, ww); R counts the atoms with w > 0.
+    int R_last = 0;  // active atoms of the last evaluated state
     auto evaluate = [&](const float *ps, const float *ww, float *c_out, double *J) -> qst_status {
         qst_status rc = qst_forward(p, ps, ww, basis, row_ptr, outcome, count, shots, nullptr, c_out, p->step_loss,
                                     nullptr, stream);
@@ -2215,6 +2225,7 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
             return QST_ERR_CUDA;
         int R = 0;
         for (int k = 0; k < K; ++k) R += wh[k] > 0.f;
+        R_last = R;
         *J = L + sp.mu * R;
         return QST_OK;
     };
@@ -2246,12 +2257,16 @@ qst_status qst_step(qst_plan p, int slot, int r, float *psi, float *w, const uin
     }
     double eta = sp.eta0;
     if (slot == 3) {  // spectral step (Sec. III-C) with eta_rho on the step grid
+        // serial-equivalent oracle calls per trial: G on every Krylov block (K vectors), the new
+        // atoms' responses and the loss
+        p->step_calls = 0;
         for (int j = 0; j < sp.n_eta; ++j, eta *= sp.eta_ratio) {
             rc = spectral_candidate(p, psi, w, row_ptr, outcome, eta, sp, p->step_trial, p->step_tw, st);
             if (rc) return rc;
             double Jt = 0.0;
             rc = evaluate(trial_psi, p->step_tw, nullptr, &Jt);
             if (rc) return rc;
+            p->step_calls += (long long)p->lz_blocks * K + R_last + 1;
             if (Jt <= J0 - sp.tau_acc) {
                 if (cudaMemcpyAsync(psi, trial_psi, sizeof(float2) * K * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
                     cudaMemcpyAsync(w, p->step_tw, sizeof(float) * K, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
@@ -2330,6 +2345,7 @@ void qst_iter_params_default(qst_iter_params *ip) {
     ip->delta_window = 20;
     ip->delta_tol = 1e-4;
     ip->max_oracle_calls = 100000;
+    ip->spectral = 0;
 }
 
 }  // extern "C"
@@ -2487,34 +2503,22 @@ qst_status iterate_sequence(qst_plan p, int T, int t0, float *psi, float *w, con
 }
 }  // namespace
 
-extern "C" {
-
-qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const uint8_t *basis, const int64_t *row_ptr,
-                       const uint32_t *outcome, const uint32_t *count, const uint32_t *shots,
-                       const qst_iter_params *params, double *J_hist, int *accepted_hist, void *stream) {
-    if (!p || T < 1 || t0 < 0 || !psi || !w || !basis || !row_ptr || !shots || !J_hist) return QST_ERR_INVALID_ARG;
-    if (p->nnz > 0 && (!outcome || !count)) return QST_ERR_INVALID_ARG;
-    if (!aligned(psi, 16) || !aligned(w, 4) || !aligned(J_hist, 8) || (accepted_hist && !aligned(accepted_hist, 4)))
-        return QST_ERR_INVALID_ARG;
-    qst_iter_params ip;
-    qst_iter_params_default(&ip);
-    if (params) ip = *params;
+namespace {
+// T iterations from t0 as one CUDA graph, captured on the first call with a
+// given key and replayed afterwards (no T_rho slot runs the spectral step here).
+qst_status iterate_graph(qst_plan p, int T, int t0, float *psi, float *w, const uint8_t *basis,
+                         const int64_t *row_ptr, const uint32_t *outcome, const uint32_t *count,
+                         const uint32_t *shots, const qst_iter_params &ip, double *J_hist, int *accepted_hist,
+                         cudaStream_t st) {
+    // the graph depends on the pointers, T, whether it starts a run, the slots and the parameters
     const qst_step_params &sp = ip.step;
-    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0) || ip.T_alpha < 0 || ip.T_ref < 0 ||
-        ip.delta_window < 0 || ip.delta_window >= kIterRing || !(ip.delta_tol >= 0.0) || ip.max_oracle_calls < 0)
-        return QST_ERR_INVALID_ARG;
-    if (p->wide || p->K > kProjMax) return QST_ERR_UNSUPPORTED;
-    for (int i = 0; i < T; ++i)
-        if (iter_slot(ip, (int64_t)t0 + i) == 2 && !p->refac_C) return QST_ERR_UNSUPPORTED;
-    cudaStream_t st = (cudaStream_t)stream;
-    // the graph depends on the pointers, T, the schedule phase of t0 and the parameters
-    const int64_t period = (int64_t)(ip.T_alpha > 0 ? ip.T_alpha : 1) * (ip.T_ref > 0 ? ip.T_ref : 1);
     std::vector<double> key = {(double)(uintptr_t)psi, (double)(uintptr_t)w, (double)(uintptr_t)basis,
                                (double)(uintptr_t)row_ptr, (double)(uintptr_t)outcome, (double)(uintptr_t)count,
                                (double)(uintptr_t)shots, (double)(uintptr_t)J_hist, (double)(uintptr_t)accepted_hist,
-                               (double)T, (double)(t0 == 0 ? -1 : t0 % period), sp.mu, sp.tau, sp.tau_acc, sp.eta0,
+                               (double)T, (double)(t0 == 0), sp.mu, sp.tau, sp.tau_acc, sp.eta0,
                                sp.eta_ratio, (double)sp.n_eta, (double)ip.T_alpha, (double)ip.T_ref,
                                (double)ip.delta_window, ip.delta_tol, (double)ip.max_oracle_calls};
+    for (int i = 0; i < T; ++i) key.push_back((double)iter_slot(ip, (int64_t)t0 + i));
     if (!p->it_exec || key != p->it_key) {
         if (p->it_exec) {
             cudaGraphExecDestroy(p->it_exec);
@@ -2553,6 +2557,100 @@ qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const ui
     const cudaError_t le = cudaGraphLaunch(p->it_exec, st);
     if (le != cudaSuccess) return graph_fail("cudaGraphLaunch", le);
     p->total_launches += p->it_launches;
+    return QST_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qst_status qst_iterate(qst_plan p, int T, int t0, float *psi, float *w, const uint8_t *basis, const int64_t *row_ptr,
+                       const uint32_t *outcome, const uint32_t *count, const uint32_t *shots,
+                       const qst_iter_params *params, double *J_hist, int *accepted_hist, void *stream) {
+    if (!p || T < 1 || t0 < 0 || !psi || !w || !basis || !row_ptr || !shots || !J_hist) return QST_ERR_INVALID_ARG;
+    if (p->nnz > 0 && (!outcome || !count)) return QST_ERR_INVALID_ARG;
+    if (!aligned(psi, 16) || !aligned(w, 4) || !aligned(J_hist, 8) || (accepted_hist && !aligned(accepted_hist, 4)))
+        return QST_ERR_INVALID_ARG;
+    qst_iter_params ip;
+    qst_iter_params_default(&ip);
+    if (params) ip = *params;
+    const qst_step_params &sp = ip.step;
+    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0) || ip.T_alpha < 0 || ip.T_ref < 0 ||
+        ip.delta_window < 0 || ip.delta_window >= kIterRing || !(ip.delta_tol >= 0.0) || ip.max_oracle_calls < 0)
+        return QST_ERR_INVALID_ARG;
+    if (p->wide || p->K > kProjMax) return QST_ERR_UNSUPPORTED;
+    if (ip.spectral != 0 && ip.spectral != 1) return QST_ERR_INVALID_ARG;
+    for (int i = 0; i < T; ++i)
+        if (iter_slot(ip, (int64_t)t0 + i) == 2 && !(ip.spectral ? p->lz_Q != nullptr : p->refac_C != nullptr))
+            return QST_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ip.spectral) return iterate_graph(p, T, t0, psi, w, basis, row_ptr, outcome, count, shots, ip, J_hist,
+                                           accepted_hist, st);
+    // T_rho slots run the spectral step (qst_step slot 3, whose Krylov block sizes the host reads):
+    // graph segments between them, the slot itself through qst_step, its outcome fed into the
+    // device state's history and stopping rules.
+    if (t0 == 0 && iter_slot(ip, 0) == 2) {  // the run starts with a T_rho slot: start the state here
+        qst_status rc = prepare(p, basis, row_ptr, outcome, shots, st);
+        if (!rc) rc = forward_core(p, psi, w, row_ptr, outcome, count, shots, nullptr, p->step_c, p->step_loss,
+                                   nullptr, nullptr, st);
+        if (!rc) rc = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_iter_init<<<1, 32, 0, st>>>(p->it_state, p->step_loss, w, p->K, sp.mu, 1);
+        });
+        if (rc) return rc;
+    }
+    // segments write their history into plan-owned buffers, so every segment with the same
+    // slots replays one graph; the history is then copied into place
+    int seg_max = 0;
+    for (int i = 0, len = 0; i < T; ++i) {
+        len = iter_slot(ip, (int64_t)t0 + i) == 2 ? 0 : len + 1;
+        seg_max = len > seg_max ? len : seg_max;
+    }
+    if (seg_max > p->it_seg_cap) {
+        cudaFree(p->it_Jseg);
+        cudaFree(p->it_aseg);
+        p->it_Jseg = nullptr;
+        p->it_aseg = nullptr;
+        p->it_seg_cap = 0;
+        if (cudaMalloc(&p->it_Jseg, sizeof(double) * seg_max) != cudaSuccess ||
+            cudaMalloc(&p->it_aseg, sizeof(int) * seg_max) != cudaSuccess) {
+            cudaGetLastError();
+            return QST_ERR_NO_MEMORY;
+        }
+        p->it_seg_cap = seg_max;
+    }
+    for (int i = 0; i < T;) {
+        int j = i;
+        while (j < T && iter_slot(ip, (int64_t)t0 + j) != 2) ++j;
+        if (j > i) {
+            qst_status rc = iterate_graph(p, j - i, t0 + i, psi, w, basis, row_ptr, outcome, count, shots, ip,
+                                          p->it_Jseg, p->it_aseg, st);
+            if (!rc && (cudaMemcpyAsync(J_hist + i, p->it_Jseg, sizeof(double) * (j - i), cudaMemcpyDeviceToDevice,
+                                        st) != cudaSuccess ||
+                        (accepted_hist && cudaMemcpyAsync(accepted_hist + i, p->it_aseg, sizeof(int) * (j - i),
+                                                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)))
+                rc = QST_ERR_CUDA;
+            if (rc) return rc;
+        }
+        if (j == T) break;
+        int stopped = 0;
+        if (cudaMemcpyAsync(&stopped, &p->it_state->stopped, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return QST_ERR_CUDA;
+        double J = 0.0, eta = 0.0;
+        int acc = 0;
+        long long calls = 0;
+        if (!stopped) {
+            const qst_status rc = qst_step(p, 3, 0, psi, w, basis, row_ptr, outcome, count, shots, &ip.step, &J, &acc,
+                                           &eta, stream);
+            if (rc) return rc;
+            calls = p->step_calls;
+        }
+        const qst_status rc = launch(p, QST_KERNEL_STEP, st, [&] {
+            k_iter_external<<<1, 32, 0, st>>>(p->it_state, J_hist, accepted_hist, j, J, acc, calls, ip.delta_window,
+                                              ip.delta_tol, ip.max_oracle_calls);
+        });
+        if (rc) return rc;
+        i = j + 1;
+    }
     return QST_OK;
 }
 

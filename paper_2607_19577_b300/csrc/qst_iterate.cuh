@@ -145,3 +145,27 @@ __global__ void k_iter_end(IterState *s, double *J_hist, int *acc_hist, int i, i
     }
     if (max_calls > 0 && s->oracle_calls >= max_calls) s->stopped = 1;
 }
+
+// An iteration run outside the graph (the spectral slot through qst_step,
+// between graph segments): its J, acceptance and serial-equivalent oracle
+// calls enter the same history and stopping rules as k_iter_end.  A run that
+// a rule has stopped records the unchanged J and no acceptance.
+__global__ void k_iter_external(IterState *s, double *J_hist, int *acc_hist, int i, double J, int accepted,
+                                long long calls, int window, double tol, long long max_calls) {
+    if (threadIdx.x | blockIdx.x) return;
+    const bool live = !s->stopped;
+    if (live && accepted) s->J = J;
+    J_hist[i] = s->J;
+    if (acc_hist) acc_hist[i] = live && accepted;
+    if (!live) return;
+    s->oracle_calls += calls;
+    if (accepted) {
+        s->n_acc += 1;
+        s->J_ring[s->n_acc % kIterRing] = s->J;
+        if (window > 0 && s->n_acc >= window) {
+            const double J0 = s->J_ring[(s->n_acc - window) % kIterRing];
+            if ((J0 - s->J) / fabs(J0) < tol) s->stopped = 1;
+        }
+    }
+    if (max_calls > 0 && s->oracle_calls >= max_calls) s->stopped = 1;
+}

@@ -51,7 +51,7 @@ class _StepParams(ctypes.Structure):
 class _IterParams(ctypes.Structure):
     _fields_ = [("step", _StepParams), ("T_alpha", ctypes.c_int), ("T_ref", ctypes.c_int),
                 ("delta_window", ctypes.c_int), ("delta_tol", ctypes.c_double),
-                ("max_oracle_calls", ctypes.c_longlong)]
+                ("max_oracle_calls", ctypes.c_longlong), ("spectral", ctypes.c_int)]
 
 
 _lib = None
@@ -334,13 +334,15 @@ class Plan:
         return J.value, bool(acc.value), eta.value
 
     def iterate(self, T, t0, psi, w, d: Data, J_hist=None, accepted=None, T_alpha=5, T_ref=50, delta_window=20,
-                delta_tol=1e-4, max_oracle_calls=100000, **step_params):
+                delta_tol=1e-4, max_oracle_calls=100000, spectral=False, **step_params):
         """qst_iterate: T iterations of Algorithm 1 from iteration t0, in place on psi
         and w, every decision on the device (one CUDA graph, replayed on later calls
         with the same buffers), with the stopping rules of Table I (delta over the
         last delta_window accepted updates below delta_tol, or max_oracle_calls
-        serial-equivalent oracle calls; 0 disables either).  Returns device tensors
-        (J_hist float64 [T], accepted int32 [T]); nothing is synchronised."""
+        serial-equivalent oracle calls; 0 disables either).  spectral: the T_rho
+        slots run the spectral step (qst_step slot 3) between graph segments, the
+        host synchronising there.  Returns device tensors (J_hist float64 [T],
+        accepted int32 [T]); nothing else is synchronised."""
         _need(psi, torch.complex64, (self.K, self.D), "psi")
         _need(w, torch.float32, (self.K,), "w")
         self._data(d)
@@ -348,6 +350,7 @@ class Plan:
         load().qst_iter_params_default(ctypes.byref(ip))
         ip.T_alpha, ip.T_ref = int(T_alpha), int(T_ref)
         ip.delta_window, ip.delta_tol, ip.max_oracle_calls = int(delta_window), float(delta_tol), int(max_oracle_calls)
+        ip.spectral = int(bool(spectral))
         for k, v in step_params.items():
             setattr(ip.step, k, v)
         J_hist = torch.empty(T, dtype=torch.float64, device="cuda") if J_hist is None else J_hist

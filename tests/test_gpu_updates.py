@@ -184,6 +184,48 @@ def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref, round
     plan.close()
 
 
+@pytest.mark.parametrize("name,K,T,T_alpha,T_ref", [("n8_m40_k4", 4, 11, 3, 4), ("n10_m60_k8", 8, 9, 4, 3)])
+def test_iterate_with_spectral_slots_equals_host_steps(name, K, T, T_alpha, T_ref):
+    """qst_iterate with spectral = 1: the T_rho slots run qst_step slot 3 between graph
+    segments (one graph replayed for segments with the same slots).  Bitwise the same
+    atoms, weights, J and acceptances as the schedule driven from the host with
+    qst_step (slot 3 at the T_rho slots), over a first run and a continued one; the
+    device's oracle-call count adds the spectral slots' calls."""
+    inst = synth.make_instance(name, seed=21, K=K)
+    psi0 = inst.psi.astype(np.complex128)
+    psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
+    psi0 = psi0.astype(np.complex64)
+    w0 = inst.w.astype(np.float32)
+    plan = qst.Plan(inst.n, inst.M, K, inst.nnz)
+    d = qst.Data.from_numpy(inst.n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    hp, hw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
+    Jh, acc_h, count = [], [], 0
+    for t in range(2 * T):
+        slot = _schedule(t, T_alpha, T_ref)
+        r = 0
+        if slot == 0:
+            act = [k for k, v in enumerate(hw.cpu().numpy()) if v > 0]
+            r = act[count % len(act)]
+            count += 1
+        J, acc, _ = plan.step(3 if slot == 2 else slot, r, hp, hw, d)
+        Jh.append(J)
+        acc_h.append(acc)
+    dp, dw = torch.from_numpy(psi0.copy()).cuda(), torch.from_numpy(w0.copy()).cuda()
+    off = dict(delta_window=0, max_oracle_calls=0)
+    J1, a1 = plan.iterate(T, 0, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref, spectral=True, **off)
+    J1, a1 = J1.cpu().numpy().copy(), a1.cpu().numpy().copy()
+    calls1 = plan.iterate_state()["oracle_calls"]
+    J2, a2 = plan.iterate(T, T, dp, dw, d, T_alpha=T_alpha, T_ref=T_ref, spectral=True, **off)
+    torch.cuda.synchronize()
+    plan.check()
+    assert [bool(x) for x in list(a1) + list(a2.cpu().numpy())] == acc_h
+    assert list(J1) + list(J2.cpu().numpy()) == Jh
+    assert torch.equal(dp, hp) and torch.equal(dw, hw)
+    assert any(acc_h[t] for t in range(2 * T) if _schedule(t, T_alpha, T_ref) == 2)
+    assert plan.iterate_state()["oracle_calls"] > calls1 > 0
+    plan.close()
+
+
 @pytest.mark.parametrize("name,K,seed,rank_fix", [("n4_all81", 4, 3, 0), ("n8_m40_k4", 4, 5, 0),
                                                   ("n10_m60_k8", 8, 7, 0), ("n8_m40_k4", 4, 5, 2),
                                                   ("n10_m60_k8", 8, 7, 3)])
