@@ -80,14 +80,74 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+    """SM clock and clock-event (throttle) reasons sampled while the timed region
+    runs: NVML every 10 ms from a thread (the device matched by PCI bus id), the
+    first sample taken before __enter__ returns; nvidia-smi every 200 ms when NVML
+    is not available.  Reading only: no setting of the GPU is changed."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.thread = None
+        self.samples = []  # (sm_mhz, sm_max_mhz, set of reasons)
         self.lines = []
+        self._stop = threading.Event()
+
+    def _nvml(self):
+        """Minimal NVML reader over ctypes (read-only queries of nvml.h): returns
+        (sm_clock(), max_sm_clock, reasons()) for the device of self.index."""
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit")
+        h = ctypes.c_void_p()
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = b"%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) != 0:
+                raise RuntimeError("by bus id")
+        except Exception:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                raise RuntimeError("by index")
+        NVML_CLOCK_SM = 1
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(mx)) != 0:
+            raise RuntimeError("max clock")
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def sm_clock():
+            v = ctypes.c_uint()
+            lib.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(v))
+            return float(v.value)
+
+        def reasons():
+            v = ctypes.c_ulonglong()
+            reasons_fn(h, ctypes.byref(v))
+            # clock-event reason bits of nvml.h
+            bits = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                    "hw_thermal_slowdown": 0x40}
+            return {k for k, b in bits.items() if v.value & b}
+        return sm_clock, float(mx.value), reasons
+
+    def _poll(self, sm_clock, mx, reasons, first):
+        while True:
+            self.samples.append((sm_clock(), mx, reasons()))
+            first.set()
+            if self._stop.wait(0.01):
+                break
 
     def __enter__(self):
+        try:
+            sm_clock, mx, reasons = self._nvml()
+            first = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(sm_clock, mx, reasons, first), daemon=True)
+            self.thread.start()
+            first.wait(timeout=2)
+            return self
+        except Exception:
+            self.thread = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
@@ -104,16 +164,22 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        self._stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.thread is not None:
             self.thread.join(timeout=2)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
+        for a, b, r in self.samples:
+            sm.append(a)
+            mx.append(b)
+            reasons |= r
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -130,7 +196,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvml, 10 ms" if self.samples else "nvidia-smi, 200 ms"}
 
 
 def kernel_source_hash():
