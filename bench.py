@@ -318,10 +318,30 @@ def batched_eval(flush, reps=10, autotune=False):
     t_graph, t_seq = timed(graph), timed(sequential)
     for p in plans:
         p.close()
+    # Algorithm 1 on every instance, one graph (qst_batch_iterate): 10 iterations of the
+    # Table I schedule from the evaluation points, capture untimed, then a timed replay
+    it_T = 10
+    ip_psis, ip_ws = [p.clone() for p in psis], [w.clone() for w in ws_]
+    Jh, acc = batch.iterate(it_T, 0, ip_psis, ip_ws, datas)
+    for p, w, p0, w0 in zip(ip_psis, ip_ws, psis, ws_):
+        p.copy_(p0)
+        w.copy_(w0)
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.iterate(it_T, 0, ip_psis, ip_ws, datas, J_hists=Jh, accepteds=acc)
+    e1.record()
+    torch.cuda.synchronize()
+    t_it = e0.elapsed_time(e1) / it_T
+    n_acc = int(sum(int(a.sum().item()) for a in acc))
     batch.close()
     out = {"workload": "64 instances, synth.make_batch(seed=0)", "amplitudes_per_eval": int(amps),
            "ms_per_eval": t_graph, "value": amps / t_graph * 1e3, "unit": "amplitudes/s",
            "sequential_ms_per_eval": t_seq, "sequential_value": amps / t_seq * 1e3,
+           "iterate": {"ms_per_iteration": t_it, "iterations": it_T, "accepted_updates": n_acc,
+                       "how": "qst_batch_iterate: every instance's Algorithm 1 sequence (Table I schedule, "
+                              "T_alpha = 5) on a forked stream of one captured graph; one timed replay"},
            "how": "qst.Batch: one launch per phase and kernel family over all instances' CTAs, captured in one "
                   "CUDA graph; sequential: one plan per instance, called in order"}
     if autotune:

@@ -421,6 +421,23 @@ qst_status qst_batch_evaluate(qst_batch batch, const float *const *psi, const fl
                               float *const *grad_w, void *stream);
 
 /*
+ * Algorithm 1 on every instance of the batch (qst_iterate per instance, in
+ * place on each instance's psi and w): each instance's iteration sequence,
+ * with its conditional trial nodes and its device stopping rules, is captured
+ * on its own forked stream into one CUDA graph on the first call with a given
+ * set of pointers, T, start (t0 == 0 or not), slots and parameters, and
+ * replayed afterwards.  Arguments are HOST arrays of `count` DEVICE pointers
+ * (J_hist[i] -> double[T], accepted_hist[i] -> int[T] or accepted_hist NULL);
+ * params as for qst_iterate (spectral must be 0: QST_ERR_INVALID_ARG).
+ * qst_iterate_state on qst_batch_plan(i) reports instance i's state.
+ */
+qst_status qst_batch_iterate(qst_batch batch, int T, int t0, float *const *psi, float *const *w,
+                             const uint8_t *const *basis, const int64_t *const *row_ptr,
+                             const uint32_t *const *outcome, const uint32_t *const *count,
+                             const uint32_t *const *shots, const qst_iter_params *params,
+                             double *const *J_hist, int *const *accepted_hist, void *stream);
+
+/*
  * Adjoint without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc.  Examples are
  * code running under an allocator it does not own (a framework's caching

@@ -2953,6 +2953,8 @@ struct qst_batch_s {
     cudaGraphExec_t exec = nullptr;
     std::vector<const void *> key;  // buffers the graph was captured with
     bool multi = false;             // every plan has a multi-instance kernel family
+    cudaGraphExec_t it_exec = nullptr;  // qst_batch_iterate's graph and its key
+    std::vector<double> it_key;
     unsigned char *dev_args = nullptr;
     size_t dev_bytes = 0;
     std::vector<BatchLaunch> launches;
@@ -2961,6 +2963,7 @@ struct qst_batch_s {
 extern "C" qst_status qst_batch_destroy(qst_batch b) {
     if (!b) return QST_ERR_INVALID_ARG;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->it_exec) cudaGraphExecDestroy(b->it_exec);
     for (auto p : b->plans)
         if (p) qst_plan_destroy(p);
     for (auto s : b->streams) cudaStreamDestroy(s);
@@ -3395,4 +3398,97 @@ extern "C" qst_status qst_batch_evaluate(qst_batch b, const float *const *psi, c
         b->key = key;
     }
     return cudaGraphLaunch(b->exec, st) == cudaSuccess ? QST_OK : QST_ERR_CUDA;
+}
+
+// Algorithm 1 on every instance of the batch: each instance's qst_iterate
+// launch sequence (with its conditional trial nodes and device stopping
+// rules) captured on its own forked stream into one CUDA graph, replayed on
+// later calls with the same pointers, T, start and parameters.
+extern "C" qst_status qst_batch_iterate(qst_batch b, int T, int t0, float *const *psi, float *const *w,
+                                        const uint8_t *const *basis, const int64_t *const *row_ptr,
+                                        const uint32_t *const *outcome, const uint32_t *const *count,
+                                        const uint32_t *const *shots, const qst_iter_params *params,
+                                        double *const *J_hist, int *const *accepted_hist, void *stream) {
+    if (!b || T < 1 || t0 < 0 || !psi || !w || !basis || !row_ptr || !outcome || !count || !shots || !J_hist)
+        return QST_ERR_INVALID_ARG;
+    qst_iter_params ip;
+    qst_iter_params_default(&ip);
+    if (params) ip = *params;
+    const qst_step_params &sp = ip.step;
+    if (sp.n_eta < 1 || !(sp.eta0 > 0.0) || !(sp.eta_ratio > 0.0) || ip.T_alpha < 0 || ip.T_ref < 0 ||
+        ip.delta_window < 0 || ip.delta_window >= kIterRing || !(ip.delta_tol >= 0.0) || ip.max_oracle_calls < 0 ||
+        ip.spectral != 0)
+        return QST_ERR_INVALID_ARG;
+    std::vector<double> key = {(double)T, (double)(t0 == 0), sp.mu, sp.tau, sp.tau_acc, sp.eta0, sp.eta_ratio,
+                               (double)sp.n_eta, (double)ip.T_alpha, (double)ip.T_ref, (double)ip.delta_window,
+                               ip.delta_tol, (double)ip.max_oracle_calls};
+    for (int t = 0; t < T; ++t) key.push_back((double)iter_slot(ip, (int64_t)t0 + t));
+    for (int i = 0; i < b->count; ++i) {
+        const qst_plan p = b->plans[i];
+        if (!psi[i] || !w[i] || !basis[i] || !row_ptr[i] || !shots[i] || !J_hist[i]) return QST_ERR_INVALID_ARG;
+        if (p->nnz > 0 && (!outcome[i] || !count[i])) return QST_ERR_INVALID_ARG;
+        if (!aligned(psi[i], 16) || !aligned(w[i], 4) || !aligned(J_hist[i], 8) ||
+            (accepted_hist && accepted_hist[i] && !aligned(accepted_hist[i], 4)))
+            return QST_ERR_INVALID_ARG;
+        if (p->wide || p->K > kProjMax) return QST_ERR_UNSUPPORTED;
+        for (int t = 0; t < T; ++t)
+            if (iter_slot(ip, (int64_t)t0 + t) == 2 && !p->refac_C) return QST_ERR_UNSUPPORTED;
+        const void *ptrs[10] = {psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i], J_hist[i],
+                                accepted_hist ? accepted_hist[i] : nullptr, nullptr};
+        for (const void *q : ptrs) key.push_back((double)(uintptr_t)q);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b->it_exec || key != b->it_key) {
+        if (b->it_exec) {
+            cudaGraphExecDestroy(b->it_exec);
+            b->it_exec = nullptr;
+        }
+        for (auto p : b->plans)
+            if (!p->it_body && cudaStreamCreateWithFlags(&p->it_body, cudaStreamNonBlocking) != cudaSuccess)
+                return QST_ERR_CUDA;
+        cudaStream_t cs = b->cap;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return QST_ERR_CUDA;
+        }
+        qst_status rc = QST_OK;
+        const int ns = (int)b->streams.size();
+        if (cudaEventRecord(b->start, cs) != cudaSuccess) rc = QST_ERR_CUDA;
+        for (int j = 0; j < ns && !rc; ++j)
+            if (cudaStreamWaitEvent(b->streams[j], b->start, 0) != cudaSuccess) rc = QST_ERR_CUDA;
+        std::vector<bool> timing(b->count);
+        std::vector<int64_t> before(b->count);
+        for (int i = 0; i < b->count && !rc; ++i) {
+            const qst_plan p = b->plans[i];
+            timing[i] = p->timing;
+            before[i] = p->total_launches;
+            p->timing = false;  // no event records inside the graph
+            rc = iterate_sequence(p, T, t0, psi[i], w[i], basis[i], row_ptr[i], outcome[i], count[i], shots[i], ip,
+                                  J_hist[i], accepted_hist ? accepted_hist[i] : nullptr, b->streams[i % ns]);
+            p->timing = timing[i];
+            p->it_launches = p->total_launches - before[i];
+            p->total_launches = before[i];
+        }
+        for (int j = 0; j < ns && !rc; ++j)
+            if (cudaEventRecord(b->join[j], b->streams[j]) != cudaSuccess ||
+                cudaStreamWaitEvent(cs, b->join[j], 0) != cudaSuccess)
+                rc = QST_ERR_CUDA;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+        if (rc || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc ? rc : QST_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&b->it_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            b->it_exec = nullptr;
+            return QST_ERR_CUDA;
+        }
+        b->it_key = key;
+    }
+    if (cudaGraphLaunch(b->it_exec, st) != cudaSuccess) return QST_ERR_CUDA;
+    for (auto p : b->plans) p->total_launches += p->it_launches;
+    return QST_OK;
 }

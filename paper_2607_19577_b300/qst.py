@@ -96,6 +96,7 @@ def load():
         lib.qst_batch_destroy.argtypes = [P]
         lib.qst_batch_plan.argtypes = [P, i32, ctypes.POINTER(P)]
         lib.qst_batch_evaluate.argtypes = [P] + [P] * 11 + [P]
+        lib.qst_batch_iterate.argtypes = [P, i32, i32] + [P] * 7 + [ctypes.POINTER(_IterParams), P, P, P]
         lib.qst_step_params_default.argtypes = [ctypes.POINTER(_StepParams)]
         lib.qst_step_params_default.restype = None
         lib.qst_step.argtypes = [P, i32, i32, P, P, P, P, P, P, P, ctypes.POINTER(_StepParams),
@@ -105,7 +106,7 @@ def load():
                      "qst_plan_kernel_stats", "qst_plan_reset_stats", "qst_plan_launch_count",
                      "qst_adjoint_noalloc", "qst_simplex_project", "qst_refactor", "qst_step",
                      "qst_batch_create", "qst_batch_create_each", "qst_batch_destroy", "qst_batch_plan",
-                     "qst_batch_evaluate"]:
+                     "qst_batch_evaluate", "qst_batch_iterate"]:
             getattr(lib, name).restype = i32
         _lib = lib
     return _lib
@@ -558,6 +559,33 @@ class Batch:
                                          ptrs([d.count for d in datas]), ptrs([d.shots for d in datas]),
                                          ptrs(losses), ptrs(c_obss), ptrs(grads), ptrs(grad_ws), _stream()),
                "qst_batch_evaluate")
+
+    def iterate(self, T, t0, psis, ws, datas, J_hists=None, accepteds=None, T_alpha=5, T_ref=50, delta_window=20,
+                delta_tol=1e-4, max_oracle_calls=100000, **step_params):
+        """qst_batch_iterate: T iterations of Algorithm 1 on every instance (lists of
+        CUDA tensors, in place on psis and ws), all instances in one CUDA graph.
+        Returns the per-instance (J_hist, accepted) device tensors."""
+        ip = _IterParams()
+        load().qst_iter_params_default(ctypes.byref(ip))
+        ip.T_alpha, ip.T_ref = int(T_alpha), int(T_ref)
+        ip.delta_window, ip.delta_tol, ip.max_oracle_calls = int(delta_window), float(delta_tol), int(max_oracle_calls)
+        for k, v in step_params.items():
+            setattr(ip.step, k, v)
+        cnt = len(self.shapes)
+        for (n, M, K, nnz), p, w in zip(self.shapes, psis, ws):
+            _need(p, torch.complex64, (K, 1 << n), "psi")
+            _need(w, torch.float32, (K,), "w")
+        J_hists = [torch.empty(T, dtype=torch.float64, device="cuda") for _ in range(cnt)] if J_hists is None else J_hists
+        accepteds = [torch.empty(T, dtype=torch.int32, device="cuda") for _ in range(cnt)] if accepteds is None \
+            else accepteds
+        P = ctypes.c_void_p * cnt
+        ptrs = lambda ts: P(*[t.data_ptr() for t in ts])  # noqa: E731
+        _check(load().qst_batch_iterate(self._h, int(T), int(t0), ptrs(psis), ptrs(ws), ptrs([d.basis for d in datas]),
+                                        ptrs([d.row_ptr for d in datas]), ptrs([d.outcome for d in datas]),
+                                        ptrs([d.count for d in datas]), ptrs([d.shots for d in datas]),
+                                        ctypes.byref(ip), ptrs(J_hists), ptrs(accepteds), _stream()),
+               "qst_batch_iterate")
+        return J_hists, accepteds
 
 
 def qst_loss(psi, w, plan: Plan, data: Data):

@@ -142,3 +142,44 @@ def test_batch_autotuner_per_size_class():
         for k in range(inst.K):
             assert np.max(np.abs(gg[k] - a["grad_psi"][k])) <= 1e-4 * np.max(np.abs(a["grad_psi"][k]))
     b.close()
+
+
+def test_batch_iterate_equals_per_instance_iterate():
+    """qst_batch_iterate (every instance's Algorithm 1 sequence on its own forked
+    stream of one captured graph) equals each instance's own qst_iterate on the
+    same plan bitwise: atoms, weights, J after every iteration, acceptances; a
+    replay of the batch graph from the same start reproduces it."""
+    insts = synth.make_batch(seed=5, count=6, n_range=(6, 12), M_range=(20, 50), shots_range=(100, 400),
+                             rank_range=(1, 3))
+    b = qst.Batch([(i.n, i.M, i.K, i.nnz) for i in insts])
+    datas = [qst.Data.from_numpy(i.n, i.basis, i.row_ptr, i.outcome, i.count, i.shots) for i in insts]
+    psi0 = []
+    for inst in insts:
+        p = inst.psi.astype(np.complex128)
+        psi0.append((p / np.linalg.norm(p, axis=1, keepdims=True)).astype(np.complex64))
+    kw = dict(T_alpha=3, T_ref=5, delta_window=0, max_oracle_calls=0)
+    T = 8
+    ps = [torch.from_numpy(p.copy()).cuda() for p in psi0]
+    ws = [torch.from_numpy(i.w.copy()).cuda() for i in insts]
+    Jb, ab = b.iterate(T, 0, ps, ws, datas, **kw)
+    torch.cuda.synchronize()
+    first = [(J.cpu().numpy().copy(), a.cpu().numpy().copy(), p.clone(), w.clone()) for J, a, p, w in zip(Jb, ab, ps, ws)]
+    for p, w, p0, inst in zip(ps, ws, psi0, insts):
+        p.copy_(torch.from_numpy(p0))
+        w.copy_(torch.from_numpy(inst.w))
+    Jb, ab = b.iterate(T, 0, ps, ws, datas, J_hists=Jb, accepteds=ab, **kw)
+    torch.cuda.synchronize()
+    for (J0, a0, p0, w0), J, a, p, w in zip(first, Jb, ab, ps, ws):
+        assert np.array_equal(J.cpu().numpy(), J0) and np.array_equal(a.cpu().numpy(), a0)
+        assert torch.equal(p, p0) and torch.equal(w, w0)
+    for idx, inst in enumerate(insts):
+        plan = b.plan(idx)
+        p = torch.from_numpy(psi0[idx].copy()).cuda()
+        w = torch.from_numpy(inst.w.copy()).cuda()
+        J, a = plan.iterate(T, 0, p, w, datas[idx], **kw)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        assert np.array_equal(J.cpu().numpy(), first[idx][0]) and np.array_equal(a.cpu().numpy(), first[idx][1])
+        assert torch.equal(p, first[idx][2]) and torch.equal(w, first[idx][3])
+    assert sum(int(f[1].sum()) for f in first) > 0
+    b.close()
