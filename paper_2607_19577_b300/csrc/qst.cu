@@ -1165,6 +1165,8 @@ struct qst_plan_s {
     int64_t ws_bytes = 0;
     // host-buffer path (allocated on first use)
     void *h_dev = nullptr;
+    cudaStream_t h_side = nullptr;  // qst_evaluate_host: the counts' copy beside the forward
+    cudaEvent_t h_fork = nullptr, h_count = nullptr;
     // accounting
     bool timing = false;
     std::vector<TimedLaunch> pending;
@@ -1477,7 +1479,8 @@ qst_status adjoint_wide(qst_plan p, const float2 *psi, const float *w, const int
 
 qst_status forward_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const uint32_t *count, const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
-                        float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache = nullptr);
+                        float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache = nullptr,
+                        cudaEvent_t count_ready = nullptr);
 qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const float *c_obs, float *grad_psi, float *grad_w, cudaStream_t st,
                         const float2 *phi_cache = nullptr, const int *skip = nullptr);
@@ -1738,6 +1741,9 @@ qst_status qst_plan_destroy(qst_plan p) {
     cudaFree(p->step_kout);
     cudaFree(p->status);
     cudaFree(p->h_dev);
+    if (p->h_side) cudaStreamDestroy(p->h_side);
+    if (p->h_fork) cudaEventDestroy(p->h_fork);
+    if (p->h_count) cudaEventDestroy(p->h_count);
     cudaFree(p->it_state);
     cudaFree(p->it_c);
     for (void *q : {(void *)p->lz_Q, (void *)p->lz_SQ, (void *)p->lz_W, (void *)p->lz_C, (void *)p->lz_P,
@@ -1806,7 +1812,8 @@ namespace {
 // (optional) every launch returns at once.
 qst_status forward_core(qst_plan p, const float *psi, const float *w, const int64_t *row_ptr, const uint32_t *outcome,
                         const uint32_t *count, const uint32_t *shots, float *p_obs, float *c_obs, double *loss,
-                        float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache) {
+                        float *p_dense, const int *skip, cudaStream_t st, float2 *phi_cache,
+                        cudaEvent_t count_ready) {
     qst_status rc = QST_OK;
     if (p_dense && cudaMemsetAsync(p_dense, 0, (size_t)p->M * ((size_t)1 << p->n) * sizeof(float), st) != cudaSuccess)
         return QST_ERR_CUDA;
@@ -1840,6 +1847,8 @@ qst_status forward_core(qst_plan p, const float *psi, const float *w, const int6
         });
         if (rc) return rc;
     }
+    // the counts are first read by the epilogue: their copy may still be in flight until here
+    if (count_ready && cudaStreamWaitEvent(st, count_ready, 0) != cudaSuccess) return QST_ERR_CUDA;
     const float invB = 1.0f / (float)p->B;
     const int egrid = p->loss_parts;
     rc = launch(p, QST_KERNEL_EPILOGUE, st, [&] {
@@ -2005,16 +2014,34 @@ qst_status qst_evaluate_host(qst_plan p, const float *psi, const float *w, const
     QST_H2D(o_basis, basis, b_basis);
     QST_H2D(o_row, row_ptr, b_row);
     QST_H2D(o_out, outcome, b_nnz);
-    QST_H2D(o_cnt, count, b_nnz);
     QST_H2D(o_shots, shots, b_shots);
 #undef QST_H2D
+    // the counts (read first by the forward's epilogue) are copied on a side stream while
+    // the packing, the validation and the forward chunk kernels run
+    if (!p->h_side && (cudaStreamCreateWithFlags(&p->h_side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&p->h_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&p->h_count, cudaEventDisableTiming) != cudaSuccess))
+        return QST_ERR_CUDA;
+    if (cudaEventRecord(p->h_fork, st) != cudaSuccess || cudaStreamWaitEvent(p->h_side, p->h_fork, 0) != cudaSuccess)
+        return QST_ERR_CUDA;
+    if (b_nnz && cudaMemcpyAsync(base + o_cnt, count, b_nnz, cudaMemcpyHostToDevice, p->h_side) != cudaSuccess)
+        return QST_ERR_CUDA;
+    if (cudaEventRecord(p->h_count, p->h_side) != cudaSuccess) return QST_ERR_CUDA;
     const float *d_psi = (const float *)(base + o_psi);
     const float *d_w = (const float *)(base + o_w);
-    qst_status rc = qst_evaluate(p, d_psi, d_w, (const uint8_t *)(base + o_basis), (const int64_t *)(base + o_row),
-                                 (const uint32_t *)(base + o_out), (const uint32_t *)(base + o_cnt),
-                                 (const uint32_t *)(base + o_shots), nullptr, (float *)(base + o_c),
-                                 (double *)(base + o_loss), (float *)(base + o_grad), (float *)(base + o_gw), stream);
-    if (rc) return rc;
+    const int64_t *d_row = (const int64_t *)(base + o_row);
+    const uint32_t *d_out = (const uint32_t *)(base + o_out);
+    qst_status rc = prepare(p, (const uint8_t *)(base + o_basis), d_row, d_out, (const uint32_t *)(base + o_shots), st);
+    if (!rc) rc = forward_core(p, d_psi, d_w, d_row, d_out, (const uint32_t *)(base + o_cnt),
+                               (const uint32_t *)(base + o_shots), nullptr, (float *)(base + o_c),
+                               (double *)(base + o_loss), nullptr, nullptr, st, p->cache_on ? p->phi : nullptr,
+                               p->h_count);
+    if (!rc) rc = adjoint_core(p, d_psi, d_w, d_row, d_out, (const float *)(base + o_c), (float *)(base + o_grad),
+                               (float *)(base + o_gw), st, p->cache_on ? p->phi : nullptr);
+    if (rc) {
+        cudaStreamSynchronize(p->h_side);
+        return rc;
+    }
     if (cudaMemcpyAsync(loss_out, base + o_loss, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return QST_ERR_CUDA;
     if (cudaMemcpyAsync(grad_psi_out, base + o_grad, b_psi, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return QST_ERR_CUDA;
