@@ -584,7 +584,7 @@ def run_ours(args):
     adj_work = inv_ops if cached else adj_ops  # the adjoint kernel's own algorithmic work
     achieved = adj_work / (adj_ms / 1e3) / 1e12
     if wide:
-        adj_kernel = ("k_adjoint_fx1c" if cached else "k_adjoint_fx1") if geo["fixed_rounds"] == 1 else "k_adjoint"
+        adj_kernel = ("k_adjoint_fx1cp" if cached else "k_adjoint_fx1p") if geo["fixed_rounds"] == 1 else "k_adjoint"
     else:
         adj_kernel = ("k_adjoint_2c" if cached else
                       {2: "k_adjoint_2r", 1: "k_adjoint_fx"}.get(geo["fixed_rounds"], "k_adjoint"))
@@ -609,7 +609,7 @@ def run_ours(args):
                                    "amplitude (the adjoint reads the forward's stored transforms)" if cached else
                                    "recomputed rotation + inverse rotation: 4 m_s + 8 FP32 lane-ops per amplitude"),
                 "launches_per_step": la / args.steps,
-                "forward": {"kernel": ("k_forward_fx1" if wide and geo["fixed_rounds"] == 1 else
+                "forward": {"kernel": ("k_forward_fx1p" if wide and geo["fixed_rounds"] == 1 else
                                        {2: "k_forward_2r", 1: "k_forward_fx"}.get(geo["fixed_rounds"], "k_forward")),
                             "ops_per_launch": fwd_ops, "ms_per_launch": ms_fwd / args.steps,
                             "achieved": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12,

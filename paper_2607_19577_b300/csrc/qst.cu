@@ -1111,6 +1111,7 @@ struct qst_plan_s {
     bool wide = false;       // n = 17..20: high bits by butterfly passes, groups of wide_G settings
     bool fx = false;         // 12-qubit chunks with fixed-position rounds (k_forward_fx / k_adjoint_fx)
     bool fx2 = false;        // 12-qubit chunks in two 6-bit rounds, two atoms per CTA (k_forward_2r / k_adjoint_2r)
+    int sms = 148;           // SMs of the plan's device (persistent grids)
     bool fw = false;         // states of 5..9 qubits in one chunk: a warp per (bin, atom) (k_forward_wu / k_adjoint_wu)
     float2 *phi = nullptr;   // [K][nnz] transform cache of qst_evaluate (two-round plans, params.phi_cache)
     bool cache_on = false;   // qst_evaluate passes phi from the forward to the adjoint
@@ -1306,9 +1307,10 @@ void launch_forward_units(qst_plan p, const FwdArgs &a0, int units, cudaStream_t
         return;
     }
     const int grid = units * p->K;
-    if (p->fx && p->wide) {  // single-setting units
-        if (a.phi_obs) k_forward_fx1<true><<<grid, kFxT, kFx1Smem, st>>>(a);
-        else k_forward_fx1<false><<<grid, kFxT, kFx1Smem, st>>>(a);
+    if (p->fx && p->wide) {  // single-setting units, persistent CTAs (three per SM)
+        const int pg = grid < 3 * p->sms ? grid : 3 * p->sms;
+        if (a.phi_obs) k_forward_fx1p<true><<<pg, kFxT, kFx1pFwdSmem, st>>>(a);
+        else k_forward_fx1p<false><<<pg, kFxT, kFx1pFwdSmem, st>>>(a);
         return;
     }
     if (p->fx) {
@@ -1348,9 +1350,14 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
         return;
     }
     const int grid = units * p->K;
-    if (p->fx && p->wide) {  // single-setting units
-        if (a.phi_obs) k_adjoint_fx1c<<<grid, kFxT, kFx1Smem, st>>>(a);
-        else k_adjoint_fx1<<<grid, kFxT, kFx1Smem, st>>>(a);
+    if (p->fx && p->wide) {  // single-setting units, persistent CTAs (four / two per SM)
+        if (a.phi_obs) {
+            const int pg = grid < 4 * p->sms ? grid : 4 * p->sms;
+            k_adjoint_fx1cp<<<pg, kFxT, kFx1pAdjcSmem, st>>>(a);
+        } else {
+            const int pg = grid < 2 * p->sms ? grid : 2 * p->sms;
+            k_adjoint_fx1p<<<pg, kFxT, kFx1pAdjSmem, st>>>(a);
+        }
         return;
     }
     if (p->fx) {
@@ -1558,6 +1565,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     cudaGetDevice(&p->device);
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    p->sms = sms;
     if (prm.max_bin_settings) {
         p->smax = prm.max_bin_settings;
     } else {
@@ -1678,10 +1686,10 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_adjoint_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, fx_smem(true).total);
         }
         if (p->wide) {
-            cudaFuncSetAttribute(k_forward_fx1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
-            cudaFuncSetAttribute(k_forward_fx1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
-            cudaFuncSetAttribute(k_adjoint_fx1, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
-            cudaFuncSetAttribute(k_adjoint_fx1c, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1Smem);
+            cudaFuncSetAttribute(k_forward_fx1p<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1pFwdSmem);
+            cudaFuncSetAttribute(k_forward_fx1p<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1pFwdSmem);
+            cudaFuncSetAttribute(k_adjoint_fx1p, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1pAdjSmem);
+            cudaFuncSetAttribute(k_adjoint_fx1cp, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1pAdjcSmem);
             cudaFuncSetAttribute(k_high_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideSmem);
             cudaFuncSetAttribute(k_high_inv_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideInvSmem);
         }
