@@ -52,8 +52,9 @@ typedef enum qst_status {
 #define QST_DEV_BAD_CSR      2  /* row_ptr / outcome malformed (range, order) */
 #define QST_DEV_BAD_SHOTS    4  /* shots[s] == 0 for a non-empty row */
 #define QST_DEV_NONFINITE    8  /* the loss is NaN or Inf */
-#define QST_DEV_TIMEOUT     16  /* a tensor-core kernel's bounded wait on its own copies or MMAs ran out
-                                   (the kernel stopped issuing work and returned; results are invalid) */
+#define QST_DEV_TIMEOUT     16  /* a kernel's bounded wait on its own bulk copies or MMAs ran out (the
+                                   tensor-core kernels, the n = 20 single-setting kernels); the kernel
+                                   stopped issuing work and returned, results are invalid */
 
 typedef struct qst_params {
     double eps;           /* epsilon of Eq. qst-loss (default 1e-8) */

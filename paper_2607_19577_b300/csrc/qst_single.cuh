@@ -1,6 +1,6 @@
-// Single-setting chunk kernels for the wide path (n = 17..20 with 12-qubit
-// chunks; included inside qst.cu's anonymous namespace, after qst_fixed.cuh
-// and qst_tensorcore.cuh).
+// Single-setting chunk kernels for the wide path with 12-qubit chunks (n = 20;
+// included inside qst.cu's anonymous namespace, after qst_fixed.cuh and
+// qst_tensorcore.cuh).
 //
 // Every wide-path unit (setting j of a group, high pattern f, atom k) carries
 // one setting, so there is nothing to amortise over settings: the source chunk

@@ -26,7 +26,7 @@ QST_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "unsupported size", 3: "CUDA error",
                 4: "out of device memory", 5: "device-side error"}
 DEV_BITS = {1: "bad basis code", 2: "malformed CSR counts", 4: "zero shots on a non-empty row",
-            8: "non-finite loss", 16: "tensor-core kernel wait timed out"}
+            8: "non-finite loss", 16: "bounded wait of a kernel on its own copies timed out"}
 KERNEL_KINDS = ["pack", "validate", "forward", "loss", "adjoint", "reduce", "hsum", "epilogue", "refactor", "step",
                 "high", "tangent"]
 
