@@ -66,9 +66,10 @@ def parse_args():
                     help="chunk transforms of two-round plans: 0 FP32 butterflies; 1..3 tensor-core products "
                          "over 6-qubit groups with the data split into that many BF16 terms (the line then also "
                          "times the FP32 plan on the same data: field vs_fp32)")
-    ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+    ap.add_argument("--fixed-rounds", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="12-qubit chunk kernels: 2 = two 6-qubit rounds, 1 = three 4-qubit rounds, "
-                         "0 = rounds chosen per setting, -1 = the plan's automatic choice")
+                         "0 = rounds chosen per setting; 3 = warp units (5..9 qubits); 4 = 16-qubit chunks on "
+                         "CTA clusters (17..20 qubits); -1 = the plan's automatic choice")
     return ap.parse_args()
 
 
@@ -568,7 +569,8 @@ def run_ours(args):
     fwd_ops, adj_ops, inv_ops = algorithmic_ops(inst.basis, K, D)
     geo = plan.geometry()
     wide = n > 16
-    cached = (geo["fixed_rounds"] == 2 and args.phi_cache != 0) or (wide and args.phi_cache == 1)
+    cluster = geo["fixed_rounds"] == 4  # 16-qubit chunks on CTA clusters: the adjoint always reads transforms
+    cached = (geo["fixed_rounds"] == 2 and args.phi_cache != 0) or (wide and args.phi_cache == 1) or cluster
     # per-step kernel time (the wide path launches its chunk kernels once per setting group)
     la, ms_adj = stats["adjoint"]
     lf, ms_fwd = stats["forward"]
@@ -583,7 +585,9 @@ def run_ours(args):
     peak_alu = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # TFLOP/s, 1 per lane-op
     adj_work = inv_ops if cached else adj_ops  # the adjoint kernel's own algorithmic work
     achieved = adj_work / (adj_ms / 1e3) / 1e12
-    if wide:
+    if cluster:
+        adj_kernel = "k_adjoint_clc"
+    elif wide:
         adj_kernel = ("k_adjoint_fx1cp" if cached else "k_adjoint_fx1p") if geo["fixed_rounds"] == 1 else "k_adjoint"
     else:
         adj_kernel = ("k_adjoint_2c" if cached else
@@ -604,14 +608,16 @@ def run_ours(args):
                 "kernel": adj_kernel,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                "(max SM clock of MEASURED_PEAKS.json)",
-                "ops_per_launch": adj_work, "ms_per_launch": adj_ms,
+                "ops_per_launch": adj_work / max(la / args.steps, 1), "ms_per_launch": adj_ms / max(la / args.steps, 1),
                 "ops_definition": ("inverse rotation, c scaling, accumulation: 2 m_s + 4 FP32 lane-ops per "
                                    "amplitude (the adjoint reads the forward's stored transforms)" if cached else
                                    "recomputed rotation + inverse rotation: 4 m_s + 8 FP32 lane-ops per amplitude"),
                 "launches_per_step": la / args.steps,
-                "forward": {"kernel": ("k_forward_fx1p" if wide and geo["fixed_rounds"] == 1 else
+                "forward": {"kernel": ("k_forward_cl" if cluster else "k_forward_fx1p" if wide and geo["fixed_rounds"] == 1 else
                                        {2: "k_forward_2r", 1: "k_forward_fx"}.get(geo["fixed_rounds"], "k_forward")),
-                            "ops_per_launch": fwd_ops, "ms_per_launch": ms_fwd / args.steps,
+                            "ops_per_launch": fwd_ops / max(lf / args.steps, 1),
+                            "ms_per_launch": ms_fwd / args.steps / max(lf / args.steps, 1),
+                            "launches_per_step": lf / args.steps,
                             "achieved": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12,
                             "frac": fwd_ops / (ms_fwd / args.steps / 1e3) / 1e12 / peak_alu},
                 "step_vs_plain_path": {

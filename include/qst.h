@@ -59,7 +59,10 @@ typedef enum qst_status {
 typedef struct qst_params {
     double eps;           /* epsilon of Eq. qst-loss (default 1e-8) */
     int norm_settings;    /* B; 0 = M (default 0) */
-    int chunk_qubits;     /* low qubits transformed on-chip per work unit; 0 = auto */
+    int chunk_qubits;     /* low qubits transformed on-chip per work unit; 0 = auto (min(n, 12) for
+                             n <= 16, n - 8 for n = 17..20).  n = 17..20 also takes 16: 16-qubit chunks
+                             on clusters of 8 CTAs (distributed shared memory between them), settings
+                             binned by the n - 16 high qubits (see fixed_rounds = 4) */
     int max_bin_settings; /* cap on settings per work bin; 0 = auto */
     int validate;         /* 1 = check basis and CSR on the device (default 1) */
     int reg_bits;         /* amplitudes per thread per round = 2^reg_bits: 4 or 5; 0 = auto */
@@ -71,19 +74,26 @@ typedef struct qst_params {
                              middle exchange).  States of 5..9 qubits held in one chunk: 3 = one
                              warp per (bin, atom), 2^(n-5) amplitudes per lane, the low five bits'
                              butterflies by lane shuffles (QST_ERR_UNSUPPORTED for other plans).
-                             0 = rounds chosen per setting (one CTA per (bin, atom)); -1 =
-                             automatic: 3 for whole states of 5..9 qubits, for 12-qubit chunks 2
-                             when a work bin may hold >= 32 settings, else 1.  Other values:
-                             QST_ERR_INVALID_ARG.  Default -1. */
+                             0 = rounds chosen per setting (one CTA per (bin, atom)).  16-qubit
+                             chunks (n = 17..20): 4 = a cluster of 8 CTAs per (bin, high pattern,
+                             atom), each CTA two 12-qubit rows in two rounds of six qubits, then a
+                             round of the top four chunk qubits over the cluster (asking for 4
+                             selects these chunks; they take no other value).  -1 = automatic: 3
+                             for whole states of 5..9 qubits, 4 for 16-qubit chunks, for 12-qubit
+                             chunks 2 when a work bin may hold >= 32 settings, else 1.  Other
+                             values: QST_ERR_INVALID_ARG.  Default -1. */
     int phi_cache;        /* qst_evaluate's transform cache: the forward stores the transform of every
                              atom at every observed outcome (K x nnz complex64, owned by the plan) and
                              the adjoint then runs its inverse rounds only (on the n = 20 path it also
-                             skips the high-bit pass before them).  Two-round plans and the n = 20
-                             path (12-qubit chunks).  1 = on (QST_ERR_UNSUPPORTED for other plans),
-                             0 = off, -1 = automatic: on for two-round plans when K x nnz x 8 bytes
-                             <= 16 GiB, off on the n = 20 path (whose adjoint recomputes the rotated
-                             amplitudes unless asked).  qst_forward and qst_adjoint never use it.
-                             Default -1. */
+                             skips the high-bit pass before them).  Two-round plans, the n = 20
+                             path (12-qubit chunks) and 16-qubit chunks.  1 = on
+                             (QST_ERR_UNSUPPORTED for other plans), 0 = off, -1 = automatic: on for
+                             two-round plans when K x nnz x 8 bytes <= 16 GiB and for 16-qubit
+                             chunks, off on the n = 20 path (whose adjoint recomputes the rotated
+                             amplitudes unless asked).  qst_forward and qst_adjoint never use it
+                             (16-qubit chunks: their adjoint kernel reads transforms, and
+                             qst_adjoint first recomputes them with the forward kernel into the
+                             plan's buffer, which those plans always hold).  Default -1. */
     int precision;        /* arithmetic of the 12-qubit chunk transforms of two-round plans (n = 12..16
                              with fixed_rounds resolving to 2).  0 = FP32 butterflies on the SIMT
                              pipes (default).  1, 2, 3 = the transform as two dense products over
@@ -110,7 +120,8 @@ const char *qst_status_string(qst_status s);
 /*
  * Create a plan for one problem shape: n qubits (1 <= n <= 20 in this build;
  * n <= 16 bins settings by their high-bit pattern, n = 17..20 applies the 8
- * high-bit factors by butterfly passes per setting group),
+ * high-bit factors by butterfly passes per setting group, or with 16-qubit
+ * chunks on CTA clusters bins settings by their n - 16 high bits),
  * M >= 1 settings, K >= 1 atoms, nnz >= 0 observed (setting, outcome) pairs.
  * Allocates the device workspace (owned by the plan, freed by
  * qst_plan_destroy) on the current CUDA device.  params may be NULL.
@@ -124,9 +135,9 @@ qst_status qst_plan_workspace_bytes(qst_plan plan, int64_t *bytes);
 
 /* The plan's chunk geometry: qubits transformed on-chip per work unit, high
  * qubits applied outside the chunk (by setting bins, or by butterfly passes
- * for n = 17..20), and which chunk kernels run: 3 = a warp per (bin, atom),
- * 2 = two 6-qubit rounds, 1 = three fixed 4-qubit rounds, 0 = rounds chosen
- * per setting.  Any output
+ * on the n = 17..20 wide path), and which chunk kernels run: 4 = 16-qubit
+ * chunks on CTA clusters, 3 = a warp per (bin, atom), 2 = two 6-qubit rounds,
+ * 1 = three fixed 4-qubit rounds, 0 = rounds chosen per setting.  Any output
  * pointer may be NULL.  Host only. */
 qst_status qst_plan_geometry(qst_plan plan, int *chunk_qubits, int *high_qubits, int *fixed_rounds);
 

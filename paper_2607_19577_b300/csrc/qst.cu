@@ -302,52 +302,57 @@ __device__ __forceinline__ void pack_body(const uint8_t *__restrict__ basis, int
         P.m = __popc(xy);
         P.key = key;
         P.pad = 0;
-        // round 0: register bits = the top A chunk bits; thread bits ascending
-        uint32_t wa = 0, wb = 0;
-        for (int j = 0; j < A; ++j) wa |= (uint32_t)(c - A + j) << (4 * j);
-        wa |= ((xy >> (c - A)) & ((1u << A) - 1u)) << 20;
-        wa |= ((y >> (c - A)) & ((1u << A) - 1u)) << 25;
-        for (int b = 0; b < tb; ++b) wb |= (uint32_t)b << (4 * b);
-        P.rdA[0] = wa;
-        P.rdB[0] = wb;
-        int nr = 1;
-        uint32_t rem = xy & ((1u << (c - A)) - 1u);
-        while (rem && nr < kMaxRounds) {
-            uint32_t chosen = 0;
-            int cnt = 0;
-            while (rem && cnt < A) {
-                chosen |= rem & (0u - rem);
-                rem &= rem - 1;
-                ++cnt;
-            }
-            uint32_t regs = chosen;
-            for (int pos = c - 1; __popc(regs) < A && pos >= 0; --pos) regs |= 1u << pos;  // identity pads
-            uint32_t word = 0, xyf = 0, yf = 0;
-            int j = 0;
-            for (uint32_t cm = regs; cm; cm &= cm - 1, ++j) {
-                const int pos = __ffs(cm) - 1;
-                word |= (uint32_t)pos << (4 * j);
-                if ((chosen >> pos) & 1u) {
-                    xyf |= 1u << j;
-                    if ((y >> pos) & 1u) yf |= 1u << j;
+        // per-round plans of the generic kernels (chunks of <= 12 bits; the
+        // cluster kernels' 16-bit chunks use the masks only)
+        int nr = 0;
+        if (c <= kMaxChunk) {
+            // round 0: register bits = the top A chunk bits; thread bits ascending
+            uint32_t wa = 0, wb = 0;
+            for (int j = 0; j < A; ++j) wa |= (uint32_t)(c - A + j) << (4 * j);
+            wa |= ((xy >> (c - A)) & ((1u << A) - 1u)) << 20;
+            wa |= ((y >> (c - A)) & ((1u << A) - 1u)) << 25;
+            for (int b = 0; b < tb; ++b) wb |= (uint32_t)b << (4 * b);
+            P.rdA[0] = wa;
+            P.rdB[0] = wb;
+            nr = 1;
+            uint32_t rem = xy & ((1u << (c - A)) - 1u);
+            while (rem && nr < kMaxRounds) {
+                uint32_t chosen = 0;
+                int cnt = 0;
+                while (rem && cnt < A) {
+                    chosen |= rem & (0u - rem);
+                    rem &= rem - 1;
+                    ++cnt;
                 }
-            }
-            // thread bits: lowest available position of each residue mod 4 first
-            uint32_t avail = ((1u << c) - 1u) & ~regs, tw = 0;
-            int b = 0;
-            for (int res = 0; res < 4 && b < tb; ++res) {
-                for (int pos = res; pos < c; pos += 4) {
-                    if ((avail >> pos) & 1u) {
-                        tw |= (uint32_t)pos << (4 * b++);
-                        avail &= ~(1u << pos);
-                        break;
+                uint32_t regs = chosen;
+                for (int pos = c - 1; __popc(regs) < A && pos >= 0; --pos) regs |= 1u << pos;  // identity pads
+                uint32_t word = 0, xyf = 0, yf = 0;
+                int j = 0;
+                for (uint32_t cm = regs; cm; cm &= cm - 1, ++j) {
+                    const int pos = __ffs(cm) - 1;
+                    word |= (uint32_t)pos << (4 * j);
+                    if ((chosen >> pos) & 1u) {
+                        xyf |= 1u << j;
+                        if ((y >> pos) & 1u) yf |= 1u << j;
                     }
                 }
+                // thread bits: lowest available position of each residue mod 4 first
+                uint32_t avail = ((1u << c) - 1u) & ~regs, tw = 0;
+                int b = 0;
+                for (int res = 0; res < 4 && b < tb; ++res) {
+                    for (int pos = res; pos < c; pos += 4) {
+                        if ((avail >> pos) & 1u) {
+                            tw |= (uint32_t)pos << (4 * b++);
+                            avail &= ~(1u << pos);
+                            break;
+                        }
+                    }
+                }
+                for (; avail && b < tb; avail &= avail - 1) tw |= (uint32_t)(__ffs(avail) - 1) << (4 * b++);
+                P.rdA[nr] = word | (xyf << 20) | (yf << 25);
+                P.rdB[nr] = tw;
+                ++nr;
             }
-            for (; avail && b < tb; avail &= avail - 1) tw |= (uint32_t)(__ffs(avail) - 1) << (4 * b++);
-            P.rdA[nr] = word | (xyf << 20) | (yf << 25);
-            P.rdB[nr] = tw;
-            ++nr;
         }
         for (int j = nr; j < kMaxRounds; ++j) P.rdA[j] = P.rdB[j] = 0;
         P.nr = nr;
@@ -572,8 +577,10 @@ __device__ __forceinline__ void build_lut(const SetPlan &P, uint32_t *lut, uint3
 // amplitude t + i 2^TB of the chunk.  U_h is the unscaled product of the
 // high-bit factors, with the same rows as the butterflies (Z factors select
 // f'_j = f_j).  Only elements I0 .. I0 + NI - 1 are built (a caller short of
-// registers builds the chunk in parts).
-template <int C, int RA, int I0 = 0, int NI = Geo<C, RA>::E>
+// registers builds the chunk in parts).  CS: the chunk's own bits when the
+// 2^C amplitudes built are one block of a larger chunk (psik then points at
+// that block inside chunk 0).
+template <int C, int RA, int I0 = 0, int NI = Geo<C, RA>::E, int CS = C>
 __device__ __forceinline__ void build_source_regs(float2 (&acc)[Geo<C, RA>::E], const float2 *__restrict__ psik,
                                                   uint32_t f, uint32_t xytop, uint32_t ytop, uint32_t tid) {
     using G = Geo<C, RA>;
@@ -593,7 +600,7 @@ __device__ __forceinline__ void build_source_regs(float2 (&acc)[Geo<C, RA>::E], 
                 ph += 2;                 // X rows [[1,1],[1,-1]]
             }
         }
-        return psik + ((size_t)fp << C) + tid;
+        return psik + ((size_t)fp << CS) + tid;
     };
     const int nidx = 1 << nx;
     int idx = 0;
@@ -695,6 +702,11 @@ struct FwdArgs {
     float2 *phi_obs = nullptr;  // optional [K][nnz]: the chunk transform of psi_k at the observed outcomes
     const unsigned char *tc_ops = nullptr;  // tensor-core kernels: the 729 group operators
     int *status = nullptr;                  // tensor-core kernels: QST_DEV_TIMEOUT
+    // cluster kernels: each (setting, high pattern)'s observed entries grouped by the CTA
+    // that holds their column (k_cl_partition)
+    const int32_t *cl_perm = nullptr;
+    const uint32_t *cl_pu = nullptr;
+    const int32_t *cl_ofs = nullptr;
 };
 
 // Forward unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -859,6 +871,9 @@ struct AdjArgs {
     const int *skip = nullptr;        // optional device flag: when set, the launch does nothing
     const unsigned char *tc_ops = nullptr;  // tensor-core kernels: the 729 group operators
     int *status = nullptr;                  // tensor-core kernels: QST_DEV_TIMEOUT
+    const int32_t *cl_perm = nullptr;       // cluster kernels, as in FwdArgs
+    const uint32_t *cl_pu = nullptr;
+    const int32_t *cl_ofs = nullptr;
 };
 
 // Adjoint unit = (bin, high pattern f, atom k).  For every setting of the bin:
@@ -1086,6 +1101,7 @@ __global__ void __launch_bounds__(256) k_loss(const double *__restrict__ loss_pa
 #include "qst_fixed.cuh"
 #include "qst_tworound.cuh"
 #include "qst_tworound_packed.cuh"
+#include "qst_cluster.cuh"
 #include "qst_warp.cuh"
 #include "qst_tensorcore.cuh"
 #include "qst_single.cuh"
@@ -1113,6 +1129,10 @@ struct qst_plan_s {
     bool fx2 = false;        // 12-qubit chunks in two 6-bit rounds, two atoms per CTA (k_forward_2r / k_adjoint_2r)
     int sms = 148;           // SMs of the plan's device (persistent grids)
     bool fw = false;         // states of 5..9 qubits in one chunk: a warp per (bin, atom) (k_forward_wu / k_adjoint_wu)
+    bool cl = false;         // n = 17..20: 16-qubit chunks on 8-CTA clusters (k_forward_cl / k_adjoint_clc)
+    int32_t *cl_perm = nullptr;   // [nnz] cluster kernels: CSR index of each entry in owner-grouped order
+    uint32_t *cl_pu = nullptr;    // [nnz] its outcome's chunk bits
+    int32_t *cl_ofs = nullptr;    // [M][2^r][kClCtas + 1] group starts within each (setting, high pattern)
     float2 *phi = nullptr;   // [K][nnz] transform cache of qst_evaluate (two-round plans, params.phi_cache)
     bool cache_on = false;   // qst_evaluate passes phi from the forward to the adjoint
     unsigned char *tc_ops = nullptr;  // precision > 0: the 729 six-qubit group operators (B operand layout)
@@ -1286,6 +1306,9 @@ void launch_forward_units(qst_plan p, const FwdArgs &a0, int units, cudaStream_t
     FwdArgs a = a0;
     a.tc_ops = p->tc_ops;
     a.status = p->status;
+    a.cl_perm = p->cl_perm;
+    a.cl_pu = p->cl_pu;
+    a.cl_ofs = p->cl_ofs;
     if (p->fx2 && p->prm.precision > 0) {
         const int grid = units * ((p->K + 1) / 2);
         if (p->prm.precision == 1) launch_forward_tc<1>(a, grid, st);
@@ -1299,6 +1322,12 @@ void launch_forward_units(qst_plan p, const FwdArgs &a0, int units, cudaStream_t
             constexpr int NB = decltype(nb)::value;
             k_forward_wu<NB><<<grid, kWuT, wu_smem(NB), st>>>(a);
         });
+        return;
+    }
+    if (p->cl) {
+        const int grid = units * p->K * kClCtas;
+        if (a.phi_obs) k_forward_cl<true><<<grid, k2T, cl_smem().total, st>>>(a);
+        else k_forward_cl<false><<<grid, k2T, cl_smem().total, st>>>(a);
         return;
     }
     if (p->fx2) {
@@ -1326,6 +1355,9 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
     AdjArgs a = a0;
     a.tc_ops = p->tc_ops;
     a.status = p->status;
+    a.cl_perm = p->cl_perm;
+    a.cl_pu = p->cl_pu;
+    a.cl_ofs = p->cl_ofs;
     if (p->fx2 && p->prm.precision > 0) {  // adjoint_core supplies the transforms
         const int grid = units * ((p->K + 1) / 2);
         if (p->prm.precision == 1) k_adjoint_tc<1><<<grid, kTcT, kTcSmemAlloc, st>>>(a);
@@ -1339,6 +1371,10 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
             constexpr int NB = decltype(nb)::value;
             k_adjoint_wu<NB><<<grid, kWuT, wu_smem(NB), st>>>(a);
         });
+        return;
+    }
+    if (p->cl) {  // adjoint_core supplies the transforms
+        k_adjoint_clc<<<units * p->K * kClCtas, k2T, cl_smem().total, st>>>(a);
         return;
     }
     if (p->fx2 && a.phi_obs) {
@@ -1380,9 +1416,15 @@ qst_status prepare(qst_plan p, const uint8_t *basis, const int64_t *row_ptr, con
     if (rc) return rc;
     const int warps_per_block = 8;
     const int grid = (p->M + warps_per_block - 1) / warps_per_block;
-    return launch(p, QST_KERNEL_VALIDATE, st, [&] {
+    rc = launch(p, QST_KERNEL_VALIDATE, st, [&] {
         k_validate<<<grid, 32 * warps_per_block, 0, st>>>(row_ptr, outcome, shots, p->M, p->nnz, p->n, p->c,
                                                           p->r, p->prm.validate, p->choff, p->status);
+    });
+    if (rc || !p->cl) return rc;
+    const int64_t pairs = (int64_t)p->M << p->r;
+    return launch(p, QST_KERNEL_VALIDATE, st, [&] {
+        k_cl_partition<<<(int)((pairs + 7) / 8), 256, 0, st>>>(row_ptr, outcome, p->choff, p->M, p->r, p->cl_perm,
+                                                               p->cl_pu, p->cl_ofs);
     });
 }
 
@@ -1532,12 +1574,16 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!(prm.eps >= 0.0) || prm.norm_settings < 0 || prm.max_bin_settings < 0) return QST_ERR_INVALID_ARG;
     if (n > 16 + 4) return QST_ERR_UNSUPPORTED;
     // n <= 16: chunk min(n, 12), up to 4 binned high bits; n = 17..20: the wide
-    // path with a chunk of n - 8 bits and 8 high bits applied by butterflies.
+    // path (chunk n - 8, the 8 high bits applied by butterfly passes) or, asked
+    // for with chunk_qubits = 16, 16-qubit chunks on thread-block clusters with
+    // n - 16 binned high bits (measured slower: 154.8 against 76.8 ms per
+    // evaluation of n = 20, M = 1024, K = 8).
     const int c_default = n <= 16 ? (n < kMaxChunk ? n : kMaxChunk) : n - kWideR;
-    int c = prm.chunk_qubits ? prm.chunk_qubits : c_default;
-    if (c < 1 || c > kMaxChunk || c > n) return QST_ERR_INVALID_ARG;
+    int c = prm.chunk_qubits ? prm.chunk_qubits : (n > 16 && prm.fixed_rounds == 4 ? kClChunk : c_default);
+    const bool cl = n > 16 && c == kClChunk;
+    if (!cl && (c < 1 || c > kMaxChunk || c > n)) return QST_ERR_INVALID_ARG;
     const int r = n - c;
-    const bool wide = r > kMaxTop;
+    const bool wide = !cl && r > kMaxTop;
     if (wide && (r != kWideR || c < 9)) return QST_ERR_UNSUPPORTED;
     if (K > 4096 || M > (1 << 24) || nnz > ((int64_t)1 << 31) - 1) return QST_ERR_UNSUPPORTED;
     qst_plan p = new (std::nothrow) qst_plan_s;
@@ -1549,6 +1595,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     p->prm = prm;
     p->c = c;
     p->r = r;
+    p->cl = cl;
     const int ra = prm.reg_bits ? prm.reg_bits : kDefaultRegBits;
     if (ra != 4 && ra != 5) {
         delete p;
@@ -1556,7 +1603,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     p->A = c < ra ? c : ra;
     p->T = 1 << (c - p->A);
-    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 3 || prm.phi_cache < -1 || prm.phi_cache > 1 ||
+    if (prm.fixed_rounds < -1 || prm.fixed_rounds > 4 || prm.phi_cache < -1 || prm.phi_cache > 1 ||
         prm.precision < 0 || prm.precision > 3) {
         delete p;
         return QST_ERR_INVALID_ARG;
@@ -1582,6 +1629,11 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // one setting each: it always runs the three-round kernels (264 against
     // 356 ms on the n = 20 workload).
     const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (p->smax >= 32 ? 2 : 1);
+    // the cluster kernels are the 16-qubit chunks' only kernels (fixed_rounds 4, or automatic)
+    if (cl != (prm.fixed_rounds == 4 || (cl && prm.fixed_rounds == -1))) {
+        delete p;
+        return QST_ERR_UNSUPPORTED;
+    }
     p->fx2 = c == 12 && fr == 2 && !wide;
     p->fx = c == 12 && p->A == 4 && (fr == 1 || (fr == 2 && wide));
     // whole states of 5..9 qubits: warp-per-unit kernels unless per-setting rounds are asked for
@@ -1594,7 +1646,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     // the cached adjoint exists for the two-round kernels and the wide path's single-setting
     // 12-qubit-chunk kernels (n = 20)
-    if (prm.phi_cache == 1 && !p->fx2 && !(wide && p->fx)) {
+    if (prm.phi_cache == 1 && !p->fx2 && !(wide && p->fx) && !cl) {
         delete p;
         return QST_ERR_UNSUPPORTED;
     }
@@ -1627,6 +1679,9 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc && wide) rc = dalloc(p, &p->wide_acc, (size_t)K * D);
     if (!rc && wide) p->zbuf = p->wide_T;
     if (!rc) rc = dalloc(p, &p->hdot, (size_t)K << c);
+    if (!rc && cl) rc = dalloc(p, &p->cl_perm, nnz);
+    if (!rc && cl) rc = dalloc(p, &p->cl_pu, nnz);
+    if (!rc && cl) rc = dalloc(p, &p->cl_ofs, (size_t)M * ((size_t)1 << r) * (kClCtas + 1));
     if (!rc && K <= kRefacMax) rc = dalloc(p, &p->refac_C, (size_t)K * K);
     if (!rc && K <= kRefacMax) rc = dalloc(p, &p->refac_T, (size_t)K * K);
     if (!rc) rc = dalloc(p, &p->step_trial, (size_t)K * D);
@@ -1637,7 +1692,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     if (!rc) rc = dalloc(p, &p->step_m1, K);
     if (!rc) rc = dalloc(p, &p->step_loss, 1);
     if (!rc) rc = dalloc(p, &p->step_kout, 1);
-    if (!rc && !wide && K <= kRefacMax / 2) {  // the spectral step needs >= 2 Krylov blocks
+    if (!rc && !wide && !cl && K <= kRefacMax / 2) {  // the spectral step needs >= 2 Krylov blocks
         const size_t nv = (size_t)(kKrylovMax + K);
         rc = dalloc(p, &p->lz_Q, nv * D);
         if (!rc) rc = dalloc(p, &p->lz_SQ, nv * D);
@@ -1658,10 +1713,12 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // recomputes by default)
     if (!rc && nnz > 0 &&
         ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30)))) ||
-         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0)))
+         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0) || cl))
         rc = dalloc(p, &p->phi, (size_t)K * nnz);
     // with precision > 0 the buffer is also the tensor-core adjoint's input when the cache is off
-    p->cache_on = p->phi && !(prm.precision > 0 && prm.phi_cache == 0);
+    // (the cluster kernels' adjoint always reads transforms: without the cache it recomputes them
+    // into the same buffer first)
+    p->cache_on = p->phi && !((prm.precision > 0 || cl) && prm.phi_cache == 0);
     if (!rc && prm.precision > 0) {
         rc = dalloc(p, &p->tc_ops, (size_t)kTcOps * kTcOpBytes);
         if (!rc) {
@@ -1692,6 +1749,11 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_adjoint_fx1cp, cudaFuncAttributeMaxDynamicSharedMemorySize, kFx1pAdjcSmem);
             cudaFuncSetAttribute(k_high_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideSmem);
             cudaFuncSetAttribute(k_high_inv_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWideInvSmem);
+        }
+        if (p->cl) {
+            cudaFuncSetAttribute(k_forward_cl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cl_smem().total);
+            cudaFuncSetAttribute(k_forward_cl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cl_smem().total);
+            cudaFuncSetAttribute(k_adjoint_clc, cudaFuncAttributeMaxDynamicSharedMemorySize, cl_smem().total);
         }
         if (p->fx2) {
             cudaFuncSetAttribute(k_forward_2r<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
@@ -1736,6 +1798,9 @@ qst_status qst_plan_destroy(qst_plan p) {
     if (!p->wide) cudaFree(p->zbuf);
     cudaFree(p->wide_T);
     cudaFree(p->wide_acc);
+    cudaFree(p->cl_perm);
+    cudaFree(p->cl_pu);
+    cudaFree(p->cl_ofs);
     cudaFree(p->hdot);
     cudaFree(p->refac_C);
     cudaFree(p->refac_T);
@@ -1794,7 +1859,7 @@ qst_status qst_plan_geometry(qst_plan p, int *chunk_qubits, int *high_qubits, in
     if (!p) return QST_ERR_INVALID_ARG;
     if (chunk_qubits) *chunk_qubits = p->c;
     if (high_qubits) *high_qubits = p->r;
-    if (fixed_rounds) *fixed_rounds = p->fw ? 3 : (p->fx2 ? 2 : (p->fx ? 1 : 0));
+    if (fixed_rounds) *fixed_rounds = p->cl ? 4 : (p->fw ? 3 : (p->fx2 ? 2 : (p->fx ? 1 : 0)));
     return QST_OK;
 }
 
@@ -1920,9 +1985,9 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
         return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w, nullptr); });
     }
     const int units = p->nb_max << p->r;
-    if (p->fx2 && p->prm.precision > 0 && !phi_cache) {
-        // the tensor-core adjoint reads transforms: recompute them with the tensor-core forward
-        // (its w |.|^2 partials go to the plan's scratch and are not read)
+    if (((p->fx2 && p->prm.precision > 0) || p->cl) && !phi_cache) {
+        // the tensor-core and cluster adjoints read transforms: recompute them with the plan's
+        // forward (its w |.|^2 partials go to the plan's scratch and are not read)
         FwdArgs f;
         f.psi = a.psi;
         f.w = w;
@@ -3069,7 +3134,7 @@ qst_status batch_create(qst_batch *out, int count, const int *n, const int *M, c
     // multi-instance launches for every plan off the wide path and off the tensor cores
     b->multi = true;
     for (auto p : b->plans)
-        if (p->wide || p->prm.precision > 0) b->multi = false;
+        if (p->wide || p->cl || p->prm.precision > 0) b->multi = false;
     if (b->multi) {
         for (auto p : b->plans) set_family_attrs(plan_family(p));
         if (cudaGetLastError() != cudaSuccess) {

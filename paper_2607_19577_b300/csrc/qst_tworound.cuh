@@ -119,13 +119,15 @@ __device__ __forceinline__ void k2_tm_st16(uint32_t taddr, const float2 (&v)[64]
 }
 // Chunk f of (U_h (x) I) psi_k in round A's layout (element i of thread t =
 // amplitude t + 64 i) -> TMEM columns 0..127, built 16 elements at a time.
-// An inactive atom (k >= K) gets zeros.
+// An inactive atom (k >= K) gets zeros.  CS > 12: one 2^12 block of a chunk
+// of CS bits (psik points at the block's offset inside chunk 0).
+template <int CS = 12>
 __device__ __forceinline__ void k2_build_source(uint32_t t_src, const float2 *psik, bool active, uint32_t f,
                                                 uint32_t xytop, uint32_t ytop, uint32_t t) {
     float2 acc[64];
 #define QST_K2_PART(Q)                                                                   \
     if (active) {                                                                        \
-        build_source_regs<12, 6, 16 * (Q), 16>(acc, psik, f, xytop, ytop, t);            \
+        build_source_regs<12, 6, 16 * (Q), 16, CS>(acc, psik, f, xytop, ytop, t);        \
     } else {                                                                             \
         _Pragma("unroll") for (int i = 0; i < 16; ++i) acc[16 * (Q) + i] = make_float2(0.f, 0.f); \
     }                                                                                    \

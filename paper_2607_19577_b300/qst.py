@@ -172,8 +172,8 @@ class Plan:
         prm.eps, prm.norm_settings, prm.chunk_qubits = float(eps), int(norm_settings), int(chunk_qubits)
         prm.max_bin_settings, prm.validate = int(max_bin_settings), int(bool(validate))
         # fixed_rounds: 12-qubit chunks 2 = two 6-qubit rounds, 1 = three 4-qubit rounds;
-        # whole states of 5..9 qubits 3 = a warp per (bin, atom); 0 = per-setting rounds,
-        # -1 = automatic (True / False mean 1 / 0)
+        # whole states of 5..9 qubits 3 = a warp per (bin, atom); n = 17..20 4 = 16-qubit
+        # chunks on CTA clusters; 0 = per-setting rounds, -1 = automatic (True / False mean 1 / 0)
         prm.reg_bits, prm.fixed_rounds = int(reg_bits), int(fixed_rounds)
         # phi_cache: qst_evaluate's transform cache (two-round plans): 1 on, 0 off, -1 automatic
         prm.phi_cache = int(phi_cache)
@@ -216,8 +216,9 @@ class Plan:
         return out
 
     def geometry(self):
-        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan (fixed_rounds: 3 = warp units,
-        2 = two 6-qubit rounds, 1 = three 4-qubit rounds, 0 = per-setting rounds)."""
+        """dict(chunk_qubits, high_qubits, fixed_rounds) of this plan (fixed_rounds: 4 = 16-qubit
+        chunks on CTA clusters, 3 = warp units, 2 = two 6-qubit rounds, 1 = three 4-qubit rounds,
+        0 = per-setting rounds)."""
         c, r, fx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().qst_plan_geometry(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(fx)), "geometry")
         return {"chunk_qubits": c.value, "high_qubits": r.value, "fixed_rounds": fx.value}

@@ -1,27 +1,77 @@
-"""The wide path (n = 17..20: chunk of n - 8 bits, 8 high bits by butterfly
-passes, settings in groups) against the FP64 oracle, and the n = 20,
-M = 1024, K = 8 workload on sampled outputs and identities."""
+"""States of 17..20 qubits against the FP64 oracle: the default wide path
+(chunk of n - 8 qubits, 8 high bits by butterfly passes, settings in groups)
+and the cluster path (chunk_qubits = 16: 16-qubit chunks on 8-CTA clusters,
+settings binned by the n - 16 high bits); and the n = 20, M = 1024, K = 8
+workload on sampled outputs and identities."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2607_19577_b300 import qst, synth
-from test_gpu_parity import compare, run_gpu, run_oracle
+from test_gpu_parity import compare, run_gpu, run_gpu_evaluate, run_oracle
 
 pytestmark = pytest.mark.gpu
+
+
+# (17, 40, 2, 3000): ~1500 outcomes per (setting, high pattern), past the 512 staged per setting
+@pytest.mark.parametrize("n,M,K,shots,seed", [(17, 6, 2, 3000, 1), (17, 40, 2, 3000, 4), (18, 4, 2, 4000, 2),
+                                              (19, 5, 3, 2000, 5), (20, 3, 2, 10000, 3)])
+def test_cluster_parity(n, M, K, shots, seed):
+    inst = synth.random_instance(n, M, K, shots, 500 + seed)
+    compare(inst, run_gpu(inst, chunk_qubits=16), run_oracle(inst))
+
+
+def test_cluster_dense_p_and_many_bins():
+    """Dense p from round C's registers; 30 settings at n = 17 fill the three
+    high-pattern bins, two of them split by max_bin_settings = 4."""
+    inst = synth.random_instance(17, 30, 1, 800, 31)
+    gpu = run_gpu(inst, dense=True, max_bin_settings=4, chunk_qubits=16)
+    compare(inst, gpu, run_oracle(inst, dense=True), dense=True)
+
+
+@pytest.mark.parametrize("n,M,K,shots,seed", [(17, 9, 3, 2000, 8), (20, 5, 2, 10000, 9)])
+def test_cluster_evaluate_equals_forward_adjoint(n, M, K, shots, seed):
+    """qst_evaluate reuses the forward's transforms; qst_adjoint recomputes them
+    with the same forward kernel: both are bitwise equal, and match the oracle."""
+    inst = synth.random_instance(n, M, K, shots, 700 + seed)
+    ev = run_gpu_evaluate(inst, chunk_qubits=16)
+    compare(inst, ev, run_oracle(inst))
+    sep = run_gpu(inst, chunk_qubits=16)
+    for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
+        assert np.array_equal(ev[key], sep[key]), key
+    assert ev["loss"] == sep["loss"]
+    off = run_gpu_evaluate(inst, phi_cache=0, chunk_qubits=16)
+    for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
+        assert np.array_equal(ev[key], off[key]), key
+
+
+def test_cluster_geometry_and_refusals():
+    plan = qst.Plan(20, 8, 2, 100, chunk_qubits=16)
+    assert plan.geometry() == {"chunk_qubits": 16, "high_qubits": 4, "fixed_rounds": 4}
+    plan.close()
+    plan = qst.Plan(20, 8, 2, 100)
+    assert plan.geometry()["chunk_qubits"] == 12 and plan.geometry()["high_qubits"] == 8
+    plan.close()
+    plan = qst.Plan(17, 8, 2, 100, fixed_rounds=4)  # fixed_rounds = 4 asks for the cluster kernels
+    assert plan.geometry() == {"chunk_qubits": 16, "high_qubits": 1, "fixed_rounds": 4}
+    plan.close()
+    with pytest.raises(qst.QSTError):
+        qst.Plan(20, 8, 2, 100, chunk_qubits=16, fixed_rounds=2)  # the cluster kernels are the 16-qubit chunks' only kernels
+    with pytest.raises(qst.QSTError):
+        qst.Plan(16, 8, 2, 100, fixed_rounds=4)  # and run only 16-qubit chunks
 
 
 @pytest.mark.parametrize("n,M,K,shots,seed", [(17, 6, 2, 3000, 1), (18, 4, 2, 4000, 2), (20, 3, 2, 10000, 3)])
 def test_wide_parity(n, M, K, shots, seed):
     inst = synth.random_instance(n, M, K, shots, 500 + seed)
-    compare(inst, run_gpu(inst), run_oracle(inst))
+    compare(inst, run_gpu(inst, chunk_qubits=n - 8), run_oracle(inst))
 
 
 def test_wide_parity_several_groups():
     """n = 17 puts 64 settings in a group; 70 settings need two groups."""
     inst = synth.random_instance(17, 70, 1, 500, 77)
-    compare(inst, run_gpu(inst), run_oracle(inst))
+    compare(inst, run_gpu(inst, chunk_qubits=9), run_oracle(inst))
 
 
 @pytest.fixture(scope="module")
@@ -95,17 +145,16 @@ def test_n20_identities(c5):
 
 @pytest.mark.parametrize("n,M,K,shots,seed", [(20, 3, 2, 10000, 12), (20, 7, 3, 3000, 13)])
 def test_wide_evaluate_with_transform_cache(n, M, K, shots, seed):
-    """The n = 20 path with the transform cache (phi_cache = 1): qst_evaluate's
+    """The wide path with the transform cache (phi_cache = 1): qst_evaluate's
     adjoint skips the group's high pass and the forward rounds; against the oracle,
-    and bitwise equal to qst_forward + qst_adjoint (which recompute).  n = 17..19
-    (chunks below 12 qubits) refuse the cache."""
-    from test_gpu_parity import run_gpu_evaluate
+    and bitwise equal to qst_forward + qst_adjoint (which recompute).  Wide plans
+    of n = 17..19 (chunks below 12 qubits) refuse the cache."""
     inst = synth.random_instance(n, M, K, shots, 600 + seed)
-    ev = run_gpu_evaluate(inst, phi_cache=1)
+    ev = run_gpu_evaluate(inst, phi_cache=1, chunk_qubits=n - 8)
     compare(inst, ev, run_oracle(inst))
-    sep = run_gpu(inst, phi_cache=1)
+    sep = run_gpu(inst, phi_cache=1, chunk_qubits=n - 8)
     for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
         assert np.array_equal(ev[key], sep[key]), key
     assert ev["loss"] == sep["loss"]
     with pytest.raises(qst.QSTError):
-        qst.Plan(17, 4, 2, 10, phi_cache=1)
+        qst.Plan(17, 4, 2, 10, phi_cache=1, chunk_qubits=9)
