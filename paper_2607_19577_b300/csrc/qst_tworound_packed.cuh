@@ -573,7 +573,12 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r_multi(const AdjArgs *__re
 // A thread scatters and stages the same entries (j = t, t + 64, ...), so its
 // own cp.async wait makes them visible to it, and the staging buffer it
 // refills for setting si + 1 was last read by itself (setting si - 1).
-constexpr int k2cStage = 512;  // observed entries per setting and atom staged by cp.async
+// Only each setting's first 32 entries are staged (the scatter reads the rest
+// from global memory): that keeps a CTA at 74,000 B of shared memory, and with
+// at most 168 registers a thread three CTAs (12 warps) share an SM.  With 512
+// entries staged (104.7 KB, two CTAs per SM) the n = 16, M = 4096, K = 16
+// launch took 5.82 ms; with 32 it takes 5.63.
+constexpr int k2cStage = 32;   // observed entries per setting and atom staged by cp.async
 struct K2cSmem {
     int work, stage_u, stage_c, stage_p, masks, meta, tmem, total;
 };
@@ -607,7 +612,7 @@ __host__ __device__ constexpr bool k2_tmem_fits() {
                     return false;
     return true;
 }
-static_assert(2 * k2cCta <= k2SmemSM && 3 * k2cCta > k2SmemSM && k2_tmem_fits(), "cached-adjoint occupancy and TMEM");
+static_assert(3 * k2cCta <= k2SmemSM && 4 * k2cCta > k2SmemSM && k2_tmem_fits(), "cached-adjoint occupancy and TMEM");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -733,10 +738,10 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
         tm_dealloc(tmem_sm[0], k2cCols);
     }
 }
-__global__ void __launch_bounds__(k2T, 2) k_adjoint_2c(const AdjArgs a) {
+__global__ void __launch_bounds__(k2T, 3) k_adjoint_2c(const AdjArgs a) {
     adjoint_2c_body(a, blockIdx.x);
 }
-__global__ void __launch_bounds__(k2T, 2) k_adjoint_2c_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
+__global__ void __launch_bounds__(k2T, 3) k_adjoint_2c_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
     const int i = multi_find(start, count, (int)blockIdx.x);
     const AdjArgs a = args[i];
     adjoint_2c_body(a, (int)blockIdx.x - start[i]);
