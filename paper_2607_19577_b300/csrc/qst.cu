@@ -1378,7 +1378,7 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
         return;
     }
     if (p->fx2 && a.phi_obs) {
-        k_adjoint_2c<<<units * ((p->K + 1) / 2), k2T, k2c_smem().total, st>>>(a);
+        k_adjoint_2c<<<units * ((p->K + 1) / 2), k2T, k2c_smem(k2cStageSingle).total, st>>>(a);
         return;
     }
     if (p->fx2) {
@@ -1758,7 +1758,7 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         if (p->fx2) {
             cudaFuncSetAttribute(k_forward_2r<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
             cudaFuncSetAttribute(k_forward_2r<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
-            cudaFuncSetAttribute(k_adjoint_2c, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem().total);
+            cudaFuncSetAttribute(k_adjoint_2c, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageSingle).total);
             cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
         }
         if (prm.precision > 0) {
@@ -3082,7 +3082,7 @@ void set_family_attrs(int fam) {
     if (fam == kFam2rCache || fam == kFam2r) {
         cudaFuncSetAttribute(k_forward_2r_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_forward_2r_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
-        cudaFuncSetAttribute(k_adjoint_2c_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem().total);
+        cudaFuncSetAttribute(k_adjoint_2c_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
         cudaFuncSetAttribute(k_adjoint_2r_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
     } else if (fam <= -15) {
         // at most 16 KB of shared memory: no attribute
@@ -3387,7 +3387,7 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
         }
         case kPhAdjoint: {
             const AdjArgs *a = static_cast<const AdjArgs *>(args);
-            if (fam == kFam2rCache) k_adjoint_2c_multi<<<grid, k2T, k2c_smem().total, st>>>(a, start, cnt);
+            if (fam == kFam2rCache) k_adjoint_2c_multi<<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
             else if (fam == kFam2r) k_adjoint_2r_multi<<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_adjoint_fx_multi<<<grid, kFxT, fx_smem(true).total, st>>>(a, start, cnt);
             else if (fam <= -15)

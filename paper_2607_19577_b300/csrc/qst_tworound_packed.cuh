@@ -573,16 +573,20 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r_multi(const AdjArgs *__re
 // A thread scatters and stages the same entries (j = t, t + 64, ...), so its
 // own cp.async wait makes them visible to it, and the staging buffer it
 // refills for setting si + 1 was last read by itself (setting si - 1).
-// Only each setting's first 32 entries are staged (the scatter reads the rest
-// from global memory): that keeps a CTA at 74,000 B of shared memory, and with
-// at most 168 registers a thread three CTAs (12 warps) share an SM.  With 512
-// entries staged (104.7 KB, two CTAs per SM) the n = 16, M = 4096, K = 16
-// launch took 5.82 ms; with 32 it takes 5.63.
-constexpr int k2cStage = 32;   // observed entries per setting and atom staged by cp.async
+// How many entries per setting are staged (the scatter reads the rest from
+// global memory) trades latency against occupancy:
+//   * k_adjoint_2c stages 32: a CTA takes 74,000 B of shared memory and, with
+//     at most 168 registers a thread, three CTAs (12 warps) share an SM.  The
+//     n = 16, M = 4096, K = 16 launch (about 120 entries per setting and
+//     chunk) takes 5.63 ms, against 5.82 with 512 staged at two CTAs per SM;
+//   * k_adjoint_2c_multi (the batch, whose settings hold up to 5000 entries
+//     per chunk) stages 512 at two CTAs per SM: 4.79 against 5.16 ms with 32.
+constexpr int k2cStageSingle = 32;  // observed entries per setting and atom staged by cp.async
+constexpr int k2cStageMulti = 512;
 struct K2cSmem {
     int work, stage_u, stage_c, stage_p, masks, meta, tmem, total;
 };
-__host__ __device__ constexpr K2cSmem k2c_smem() {
+__host__ __device__ constexpr K2cSmem k2c_smem(int k2cStage) {
     K2cSmem sp{};
     sp.work = 0;
     sp.stage_p = sp.work + 2 * k2pBuf * 4;                 // [atom][buffer][entry] float2
@@ -594,11 +598,14 @@ __host__ __device__ constexpr K2cSmem k2c_smem() {
     sp.total = sp.tmem + 16;
     return sp;
 }
-static_assert(k2c_smem().stage_p % 16 == 0 && k2c_smem().stage_u % 16 == 0 && k2c_smem().stage_c % 16 == 0 &&
-                  k2c_smem().masks % 16 == 0 && k2c_smem().meta % 16 == 0,
-              "aligned shared arrays");
+__host__ __device__ constexpr bool k2c_aligned(int st) {
+    return k2c_smem(st).stage_p % 16 == 0 && k2c_smem(st).stage_u % 16 == 0 && k2c_smem(st).stage_c % 16 == 0 &&
+           k2c_smem(st).masks % 16 == 0 && k2c_smem(st).meta % 16 == 0;
+}
+static_assert(k2c_aligned(k2cStageSingle) && k2c_aligned(k2cStageMulti), "aligned shared arrays");
 constexpr uint32_t k2cCols = 128;  // TMEM columns of a cached-adjoint CTA: the accumulator
-constexpr int k2cCta = k2c_smem().total + 1024;
+constexpr int k2cCta = k2c_smem(k2cStageSingle).total + 1024;
+constexpr int k2cCtaMulti = k2c_smem(k2cStageMulti).total + 1024;
 // Every mix of two-round forward, adjoint and cached-adjoint CTAs that shared
 // memory admits on one SM fits in its 512 TMEM columns, so an allocation never
 // waits (CTAs of different kernels share an SM when the batched graph runs
@@ -606,22 +613,26 @@ constexpr int k2cCta = k2c_smem().total + 1024;
 __host__ __device__ constexpr bool k2_tmem_fits() {
     for (int na = 0; na <= 4; ++na)
         for (int nc = 0; nc <= 4; ++nc)
-            for (int nf = 0; nf <= 4; ++nf)
-                if (na * k2CtaAdj + nc * k2cCta + nf * k2CtaFwd <= k2SmemSM &&
-                    na * (int)k2ColsAdj + nc * (int)k2cCols + nf * (int)k2ColsFwd > 512)
-                    return false;
+            for (int nm = 0; nm <= 4; ++nm)
+                for (int nf = 0; nf <= 4; ++nf)
+                    if (na * k2CtaAdj + nc * k2cCta + nm * k2cCtaMulti + nf * k2CtaFwd <= k2SmemSM &&
+                        na * (int)k2ColsAdj + (nc + nm) * (int)k2cCols + nf * (int)k2ColsFwd > 512)
+                        return false;
     return true;
 }
-static_assert(3 * k2cCta <= k2SmemSM && 4 * k2cCta > k2SmemSM && k2_tmem_fits(), "cached-adjoint occupancy and TMEM");
+static_assert(3 * k2cCta <= k2SmemSM && 4 * k2cCta > k2SmemSM && 2 * k2cCtaMulti <= k2SmemSM &&
+                  3 * k2cCtaMulti > k2SmemSM && k2_tmem_fits(),
+              "cached-adjoint occupancy and TMEM");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
+template <int k2cStage>
 __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
-    constexpr K2cSmem sp = k2c_smem();
+    constexpr K2cSmem sp = k2c_smem(k2cStage);
     extern __shared__ __align__(16) unsigned char smem[];
     uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
@@ -739,10 +750,10 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
     }
 }
 __global__ void __launch_bounds__(k2T, 3) k_adjoint_2c(const AdjArgs a) {
-    adjoint_2c_body(a, blockIdx.x);
+    adjoint_2c_body<k2cStageSingle>(a, blockIdx.x);
 }
-__global__ void __launch_bounds__(k2T, 3) k_adjoint_2c_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
+__global__ void __launch_bounds__(k2T, 2) k_adjoint_2c_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
     const int i = multi_find(start, count, (int)blockIdx.x);
     const AdjArgs a = args[i];
-    adjoint_2c_body(a, (int)blockIdx.x - start[i]);
+    adjoint_2c_body<k2cStageMulti>(a, (int)blockIdx.x - start[i]);
 }
