@@ -71,7 +71,11 @@ typedef struct qst_params {
                              setting in the forward, two in the adjoint; n <= 16 only, n = 17..20
                              runs 1); 1 = three rounds of four qubits on fixed qubit groups, 16
                              amplitudes per thread (compile-time shared-memory offsets, warp-local
-                             middle exchange).  States of 5..9 qubits held in one chunk: 3 = one
+                             middle exchange).  Whole states of 10, 11 qubits: 2 = the same two
+                             rounds with 2^(n-6) threads per atom (2^(13-n) atoms per CTA); their
+                             adjoint works from the forward's transforms (the plan always holds
+                             the K x nnz buffer; qst_adjoint recomputes them with the forward).
+                             States of 5..9 qubits held in one chunk: 3 = one
                              warp per (bin, atom), 2^(n-5) amplitudes per lane, the low five bits'
                              butterflies by lane shuffles (QST_ERR_UNSUPPORTED for other plans).
                              0 = rounds chosen per setting (one CTA per (bin, atom)).  16-qubit
@@ -79,7 +83,8 @@ typedef struct qst_params {
                              atom), each CTA two 12-qubit rows in two rounds of six qubits, then a
                              round of the top four chunk qubits over the cluster (asking for 4
                              selects these chunks; they take no other value).  -1 = automatic: 3
-                             for whole states of 5..9 qubits, 4 for 16-qubit chunks, for 12-qubit
+                             for whole states of 5..9 qubits, 4 for 16-qubit chunks, for whole
+                             states of 10, 11 qubits 2 when nnz <= M 2^n / 4 else 0, for 12-qubit
                              chunks 2 when a work bin may hold >= 32 settings, else 1.  Other
                              values: QST_ERR_INVALID_ARG.  Default -1. */
     int phi_cache;        /* qst_evaluate's transform cache: the forward stores the transform of every

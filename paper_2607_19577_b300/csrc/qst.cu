@@ -1331,8 +1331,12 @@ void launch_forward_units(qst_plan p, const FwdArgs &a0, int units, cudaStream_t
         return;
     }
     if (p->fx2) {
-        if (a.phi_obs) k_forward_2r<true><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
-        else k_forward_2r<false><<<units * ((p->K + 1) / 2), k2T, k2_smem_fwd().total, st>>>(a);
+        const int grid = units * k2_atom_groups(p->K, p->c);
+        with_chunk2(p->c, [&](auto cc) {
+            constexpr int C = decltype(cc)::value;
+            if (a.phi_obs) k_forward_2r<true, C><<<grid, k2T, k2_smem_fwd().total, st>>>(a);
+            else k_forward_2r<false, C><<<grid, k2T, k2_smem_fwd().total, st>>>(a);
+        });
         return;
     }
     const int grid = units * p->K;
@@ -1378,7 +1382,11 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
         return;
     }
     if (p->fx2 && a.phi_obs) {
-        k_adjoint_2c<<<units * ((p->K + 1) / 2), k2T, k2c_smem(k2cStageSingle).total, st>>>(a);
+        const int grid = units * k2_atom_groups(p->K, p->c);
+        with_chunk2(p->c, [&](auto cc) {
+            constexpr int C = decltype(cc)::value;
+            k_adjoint_2c<C><<<grid, k2T, k2c_smem(k2cStageSingle).total, st>>>(a);
+        });
         return;
     }
     if (p->fx2) {
@@ -1628,13 +1636,21 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // bin measured ~20 % faster with three rounds).  The wide path's units hold
     // one setting each: it always runs the three-round kernels (264 against
     // 356 ms on the n = 20 workload).
-    const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (p->smax >= 32 ? 2 : 1);
+    // Whole states of 10, 11 qubits: the two-round kernels (their adjoint reads
+    // the forward's transforms, 8 bytes per observed entry and atom) when at most
+    // a quarter of the outcomes are observed, else the per-setting-round kernels:
+    // n = 11, M = 2000, K = 8 took 0.349 against 0.412 ms per evaluation at 200
+    // shots a setting, 1.07 against 0.71 ms at 5000 (about 1800 of 2048 observed).
+    const bool sparse = (int64_t)nnz * 4 <= ((int64_t)M << c);
+    const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds
+                                         : (c < 12 && r == 0 && c >= 10 ? (sparse ? 2 : 0) : (p->smax >= 32 ? 2 : 1));
     // the cluster kernels are the 16-qubit chunks' only kernels (fixed_rounds 4, or automatic)
     if (cl != (prm.fixed_rounds == 4 || (cl && prm.fixed_rounds == -1))) {
         delete p;
         return QST_ERR_UNSUPPORTED;
     }
-    p->fx2 = c == 12 && fr == 2 && !wide;
+    // two-round kernels: 12-qubit chunks, and whole states of 10, 11 qubits (chunks of 10, 11)
+    p->fx2 = (c == 12 || (c >= 10 && c < 12 && r == 0)) && fr == 2 && !wide && !cl;
     p->fx = c == 12 && p->A == 4 && (fr == 1 || (fr == 2 && wide));
     // whole states of 5..9 qubits: warp-per-unit kernels unless per-setting rounds are asked for
     // (0); from 10 qubits on a lane's 32 amplitudes and accumulator need ~250 registers and the
@@ -1650,8 +1666,8 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         delete p;
         return QST_ERR_UNSUPPORTED;
     }
-    // the tensor-core chunk transforms exist for the two-round plans
-    if (prm.precision > 0 && !p->fx2) {
+    // the tensor-core chunk transforms exist for the two-round plans of 12-qubit chunks
+    if (prm.precision > 0 && !(p->fx2 && c == 12)) {
         delete p;
         return QST_ERR_UNSUPPORTED;
     }
@@ -1713,12 +1729,13 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // recomputes by default)
     if (!rc && nnz > 0 &&
         ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30)))) ||
-         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0) || cl))
+         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0) || cl || (p->fx2 && c < 12)))
         rc = dalloc(p, &p->phi, (size_t)K * nnz);
     // with precision > 0 the buffer is also the tensor-core adjoint's input when the cache is off
     // (the cluster kernels' adjoint always reads transforms: without the cache it recomputes them
     // into the same buffer first)
-    p->cache_on = p->phi && !((prm.precision > 0 || cl) && prm.phi_cache == 0);
+    // (the same for the two-round kernels of 10- and 11-qubit chunks, which have no recomputing adjoint)
+    p->cache_on = p->phi && !((prm.precision > 0 || cl || (p->fx2 && c < 12)) && prm.phi_cache == 0);
     if (!rc && prm.precision > 0) {
         rc = dalloc(p, &p->tc_ops, (size_t)kTcOps * kTcOpBytes);
         if (!rc) {
@@ -1758,7 +1775,13 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
         if (p->fx2) {
             cudaFuncSetAttribute(k_forward_2r<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
             cudaFuncSetAttribute(k_forward_2r<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
-            cudaFuncSetAttribute(k_adjoint_2c, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageSingle).total);
+            cudaFuncSetAttribute(k_adjoint_2c<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageSingle).total);
+            cudaFuncSetAttribute(k_adjoint_2c<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageSingle).total);
+            cudaFuncSetAttribute(k_adjoint_2c<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageSingle).total);
+            cudaFuncSetAttribute(k_forward_2r<false, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+            cudaFuncSetAttribute(k_forward_2r<true, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+            cudaFuncSetAttribute(k_forward_2r<false, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+            cudaFuncSetAttribute(k_forward_2r<true, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
             cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
         }
         if (prm.precision > 0) {
@@ -1985,7 +2008,7 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
         return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w, nullptr); });
     }
     const int units = p->nb_max << p->r;
-    if (((p->fx2 && p->prm.precision > 0) || p->cl) && !phi_cache) {
+    if (((p->fx2 && (p->prm.precision > 0 || p->c < 12)) || p->cl) && !phi_cache) {
         // the tensor-core and cluster adjoints read transforms: recompute them with the plan's
         // forward (its w |.|^2 partials go to the plan's scratch and are not read)
         FwdArgs f;
@@ -3014,9 +3037,11 @@ __global__ void __launch_bounds__(256) k_hsum_multi(const HsumArgs *__restrict__
 // Chunk-kernel family of a plan: the multi-instance forward / adjoint
 // launches group instances by it (same kernel, block and shared memory).
 // >= 0: generic kernels, 100 c + A; -10 - n: warp-unit kernels of n qubits
-enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3 };
+enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3, kFam2rCache11 = -4, kFam2rCache10 = -5 };
 int plan_family(const qst_plan_s *p) {
     if (p->fw) return -10 - p->n;
+    if (p->fx2 && p->c == 11) return kFam2rCache11;  // (such plans join a batch's launches with their cache on)
+    if (p->fx2 && p->c == 10) return kFam2rCache10;
     if (p->fx2) return p->cache_on ? kFam2rCache : kFam2r;
     if (p->fx) return kFamFx;
     return 100 * p->c + p->A;
@@ -3025,7 +3050,7 @@ int plan_family(const qst_plan_s *p) {
 int64_t plan_unit_ctas(const qst_plan_s *p) {
     const int64_t units = (int64_t)p->nb_max << p->r;
     if (p->fw) return (units * p->K + kWuT / 32 - 1) / (kWuT / 32);
-    return units * (p->fx2 ? (p->K + 1) / 2 : p->K);
+    return units * (p->fx2 ? k2_atom_groups(p->K, p->c) : p->K);
 }
 
 constexpr int kBatchStreams = 16;
@@ -3082,8 +3107,14 @@ void set_family_attrs(int fam) {
     if (fam == kFam2rCache || fam == kFam2r) {
         cudaFuncSetAttribute(k_forward_2r_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_forward_2r_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
-        cudaFuncSetAttribute(k_adjoint_2c_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
+        cudaFuncSetAttribute(k_adjoint_2c_multi<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
         cudaFuncSetAttribute(k_adjoint_2r_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+    } else if (fam == kFam2rCache11) {
+        cudaFuncSetAttribute(k_forward_2r_multi<true, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+        cudaFuncSetAttribute(k_adjoint_2c_multi<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
+    } else if (fam == kFam2rCache10) {
+        cudaFuncSetAttribute(k_forward_2r_multi<true, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+        cudaFuncSetAttribute(k_adjoint_2c_multi<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
     } else if (fam <= -15) {
         // at most 16 KB of shared memory: no attribute
     } else if (fam == kFamFx) {
@@ -3134,7 +3165,7 @@ qst_status batch_create(qst_batch *out, int count, const int *n, const int *M, c
     // multi-instance launches for every plan off the wide path and off the tensor cores
     b->multi = true;
     for (auto p : b->plans)
-        if (p->wide || p->cl || p->prm.precision > 0) b->multi = false;
+        if (p->wide || p->cl || p->prm.precision > 0 || (p->fx2 && p->c < 12 && !p->cache_on)) b->multi = false;
     if (b->multi) {
         for (auto p : b->plans) set_family_attrs(plan_family(p));
         if (cudaGetLastError() != cudaSuccess) {
@@ -3372,6 +3403,8 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
             const FwdArgs *a = static_cast<const FwdArgs *>(args);
             if (fam == kFam2rCache) k_forward_2r_multi<true><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFam2r) k_forward_2r_multi<false><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
+            else if (fam == kFam2rCache11) k_forward_2r_multi<true, 11><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
+            else if (fam == kFam2rCache10) k_forward_2r_multi<true, 10><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_forward_fx_multi<<<grid, kFxT, fx_smem(false).total, st>>>(a, start, cnt);
             else if (fam <= -15)
                 with_wu(-10 - fam, [&](auto nb) {
@@ -3387,7 +3420,9 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
         }
         case kPhAdjoint: {
             const AdjArgs *a = static_cast<const AdjArgs *>(args);
-            if (fam == kFam2rCache) k_adjoint_2c_multi<<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
+            if (fam == kFam2rCache) k_adjoint_2c_multi<12><<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
+            else if (fam == kFam2rCache11) k_adjoint_2c_multi<11><<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
+            else if (fam == kFam2rCache10) k_adjoint_2c_multi<10><<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
             else if (fam == kFam2r) k_adjoint_2r_multi<<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_adjoint_fx_multi<<<grid, kFxT, fx_smem(true).total, st>>>(a, start, cnt);
             else if (fam <= -15)

@@ -317,7 +317,7 @@ __global__ void __cluster_dims__(kClCtas, 1, 1) __launch_bounds__(k2T, 3) k_forw
     const float wkk = a.w[k];
     float *pk = a.ppart + (size_t)k * a.nnz;
     issue(0);
-    k2_build_source<kClChunk>(t_src, a.psi + (size_t)un.bin * a.src_bin_stride + (size_t)k * D + ((size_t)Mrow << 12),
+    k2_build_source<12, kClChunk>(t_src, a.psi + (size_t)un.bin * a.src_bin_stride + (size_t)k * D + ((size_t)Mrow << 12),
                               true, f, b.xytop, b.ytop, t);
     tm_wait_st();
     for (int si = 0; si < bcount; ++si) {

@@ -7,6 +7,16 @@
 //   round A: chunk bits 6..11 in registers (element i = hi), thread t = lo
 //   round B: chunk bits 0..5  in registers (element j = lo), thread t = hi
 //
+// Chunks of C = 10 or 11 qubits (whole states of 10, 11 qubits) keep 64
+// amplitudes per thread with 2^(C-6) threads per atom (TA = C - 6 thread
+// bits), so a CTA of 128 threads runs 2^(13-C) atoms:
+//
+//   round A: chunk bits TA..TA+5 in registers (element i), thread t = bits
+//            0..TA-1 (amplitude t + 2^TA i); it transforms bits 6..C-1 only
+//   round B: chunk bits 0..5 in registers, thread t = bits 6..C-1
+//
+// (chunk bits TA..5 sit in both rounds' registers; round B transforms them).
+// The exchange buffer keeps u at row u / 64, column u mod 64.
 // so the forward pass needs one shared-memory exchange per setting (A -> B)
 // and the adjoint two (A -> B after the forward round A, B -> A before the
 // inverse round A), half of what three 4-bit rounds need.  A CTA runs two
@@ -118,16 +128,16 @@ __device__ __forceinline__ void k2_tm_st16(uint32_t taddr, const float2 (&v)[64]
     tm_st(taddr + 32u * Q, r);
 }
 // Chunk f of (U_h (x) I) psi_k in round A's layout (element i of thread t =
-// amplitude t + 64 i) -> TMEM columns 0..127, built 16 elements at a time.
-// An inactive atom (k >= K) gets zeros.  CS > 12: one 2^12 block of a chunk
-// of CS bits (psik points at the block's offset inside chunk 0).
-template <int CS = 12>
+// amplitude t + 2^(C-6) i) -> TMEM columns 0..127, built 16 elements at a time.
+// An inactive atom (k >= K) gets zeros.  CS > C: one 2^C block of a chunk of
+// CS bits (psik points at the block's offset inside chunk 0).
+template <int C = 12, int CS = C>
 __device__ __forceinline__ void k2_build_source(uint32_t t_src, const float2 *psik, bool active, uint32_t f,
                                                 uint32_t xytop, uint32_t ytop, uint32_t t) {
     float2 acc[64];
 #define QST_K2_PART(Q)                                                                   \
     if (active) {                                                                        \
-        build_source_regs<12, 6, 16 * (Q), 16, CS>(acc, psik, f, xytop, ytop, t);        \
+        build_source_regs<C, 6, 16 * (Q), 16, CS>(acc, psik, f, xytop, ytop, t);         \
     } else {                                                                             \
         _Pragma("unroll") for (int i = 0; i < 16; ++i) acc[16 * (Q) + i] = make_float2(0.f, 0.f); \
     }                                                                                    \
@@ -179,6 +189,21 @@ __device__ __forceinline__ void butterfly_herm(float2 (&v)[1 << A], uint32_t xyf
     }
 }
 
+// CTAs per (bin, high pattern) unit of a two-round plan: 2^(13 - c) atoms per CTA.
+inline int k2_atom_groups(int K, int c) {
+    const int apc = k2T >> (c - 6);
+    return (K + apc - 1) / apc;
+}
+// Calls fn(integral_constant<C>) for a two-round plan's chunk (10, 11, 12 qubits).
+template <typename Fn>
+void with_chunk2(int c, Fn &&fn) {
+    switch (c) {
+        case 10: fn(std::integral_constant<int, 10>()); break;
+        case 11: fn(std::integral_constant<int, 11>()); break;
+        default: fn(std::integral_constant<int, 12>()); break;
+    }
+}
+
 // Exchange A -> B: element i of thread t (= lo) goes to 66 i + t; round B
 // reads elements 2 jj, 2 jj + 1 of thread t (= hi) at 66 t + 2 jj as one
 // float4; the cached forward writes its round-B values back to the same
@@ -186,6 +211,32 @@ __device__ __forceinline__ void butterfly_herm(float2 (&v)[1 << A], uint32_t xyf
 __device__ __forceinline__ void k2_store_A(const float2 (&v)[64], float2 *wk, uint32_t t) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) wk[k2Row * i + t] = v[i];
+}
+// The same for TA = C - 6 thread bits: element i of thread t is u = t + 2^TA i.
+template <int TA>
+__device__ __forceinline__ void k2_store_A_g(const float2 (&v)[64], float2 *wk, uint32_t t) {
+    if constexpr (TA == 6) {
+        k2_store_A(v, wk, t);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) wk[k2Row * ((i << TA) >> 6) + ((i << TA) & 63) + t] = v[i];
+    }
+}
+// Round A's butterflies act on chunk bits 6..C-1: register bits 6-TA..5 of
+// the element index (bits TA..5 are round B's).
+template <int TA>
+__device__ __forceinline__ uint32_t k2_maskA(uint32_t mask) {
+    return ((mask >> TA) & 63u) & ~((1u << (6 - TA)) - 1u);
+}
+// Barrier of one atom's 2^TA threads: a named barrier of 64 (TA = 6), else
+// the atom's lanes of its warp (TA <= 5: an atom lies inside one warp, and
+// an inactive atom's lanes may skip the loop that waits here).
+template <int TA>
+__device__ __forceinline__ void k2_bar_atom_g(uint32_t ai) {
+    static_assert(TA >= 4 && TA <= 6, "chunks of 10..12 qubits");
+    if constexpr (TA == 6) k2_bar_atom(ai);
+    else if constexpr (TA == 5) __syncwarp();
+    else __syncwarp(0xffffu << (16u * (ai & 1u)));
 }
 __device__ __forceinline__ void k2_store_B(const float2 (&v)[64], float2 *wk, uint32_t t) {
     float4 *w4 = reinterpret_cast<float4 *>(wk + k2Row * t);
@@ -216,16 +267,18 @@ __device__ __forceinline__ void k2_load_B(float2 (&v)[64], const float2 *wk, uin
 // complex numbers instead (each thread rewrites only its own row, which only
 // it read), and the gather also stores them, unscaled, at the observed
 // outcomes into the atom's slice of a.phi_obs, for the cached adjoint.
-template <bool CACHE>
+// C < 12: 2^(13-C) atoms per CTA (the "two atoms" above become that many).
+template <bool CACHE, int C = 12>
 __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) {
+    constexpr int TA = C - 6, APC = k2T >> TA;  // thread bits per atom, atoms per CTA
     constexpr K2Smem sp = k2_smem_fwd();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem + sp.stage);
     uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
-    const int KP = (a.K + 1) >> 1;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & ((1u << TA) - 1u), half = tid >> TA;
+    const int KP = (a.K + APC - 1) / APC;
     const int unit = cta;
     const int kp = unit % KP;
     const int rest = unit / KP;
@@ -234,11 +287,11 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
     if (bin >= *a.n_bins || (a.skip && *a.skip)) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
-    const int k = 2 * kp + (int)half;
+    const int k = APC * kp + (int)half;
     const bool active = k < a.K;
-    float2 *wk = reinterpret_cast<float2 *>(smem + sp.work) + half * k2Buf;
+    float2 *wk = reinterpret_cast<float2 *>(smem + sp.work) + half * (k2Row << TA);
     float *pb = reinterpret_cast<float *>(wk);  // w |.|^2 at k2_fpos(u), after the exchange
-    constexpr uint32_t cmask = 4095u;
+    constexpr uint32_t cmask = (1u << C) - 1u;
     if (warp == 0) tm_alloc(tmem_sm, k2ColsFwd);
     fx_stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, masks_sm, meta_sm);
     tm_fence_before();
@@ -259,8 +312,8 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
     const float wkk = active ? a.w[k] : 0.f;
     float *pk = a.ppart + (size_t)(active ? k : 0) * a.nnz;
     issue(0);
-    k2_build_source(t_src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)(active ? k : 0) * D, active, f, b.xytop,
-                    b.ytop, t);
+    k2_build_source<C>(t_src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)(active ? k : 0) * D, active, f,
+                       b.xytop, b.ytop, t);
     tm_wait_st();
     for (int si = 0; si < bcount; ++si) {
         const uint2 mk = masks_sm[si];
@@ -271,11 +324,10 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
         // round unrolled twice does not fit the instruction cache
 #pragma unroll 1
         for (int R = 0; R < 2; ++R) {
-            const uint32_t sh = R ? 0u : 6u;
-            butterfly_herm<6>(v, (mk.x >> sh) & 63u, (mk.y >> sh) & 63u);
+            butterfly_herm<6>(v, R ? (mk.x & 63u) : k2_maskA<TA>(mk.x), R ? (mk.y & 63u) : k2_maskA<TA>(mk.y));
             if (R == 0) {
-                k2_store_A(v, wk, t);
-                k2_bar_atom(half);
+                k2_store_A_g<TA>(v, wk, t);
+                k2_bar_atom_g<TA>(half);
                 k2_load_B(v, wk, t);
             }
         }
@@ -283,7 +335,7 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
         if (CACHE) {
             k2_store_B(v, wk, t);
         } else {
-            k2_bar_atom(half);  // every round-B read of the exchange buffer is done
+            k2_bar_atom_g<TA>(half);  // every round-B read of the exchange buffer is done
             float4 *p4 = reinterpret_cast<float4 *>(pb + k2FRow * t);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -303,7 +355,7 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
         const uint32_t *st = stage + (si & 1) * k2Stage;
         if (active && CACHE) {
             float2 *phk = a.phi_obs + (size_t)k * a.nnz;
-            for (int j = t; j < mt.cnt; j += 64) {
+            for (int j = t; j < mt.cnt; j += (1 << TA)) {
                 const uint32_t u = (j < k2Stage ? st[j] : outcome[mt.lo + j]) & cmask;
                 const float2 ph = wk[k2Row * (u >> 6) + (u & 63u)];
                 pk[mt.lo + j] = scaled_abs2(sc, ph);
@@ -311,24 +363,24 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
             }
             if (a.p_dense) {
                 const int s = a.order[b.start + si];
-                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << 12);
-                for (uint32_t u = t; u <= cmask; u += 64) {
+                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
+                for (uint32_t u = t; u <= cmask; u += (1u << TA)) {
                     const float2 ph = wk[k2Row * (u >> 6) + (u & 63u)];
                     atomicAdd(pd + u, scaled_abs2(sc, ph));
                 }
             }
         } else if (active) {
-            for (int j = t; j < mt.cnt; j += 64) {
+            for (int j = t; j < mt.cnt; j += (1 << TA)) {
                 const uint32_t u = (j < k2Stage ? st[j] : outcome[mt.lo + j]) & cmask;
                 pk[mt.lo + j] = pb[k2_fpos(u)];
             }
             if (a.p_dense) {
                 const int s = a.order[b.start + si];
-                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << 12);
-                for (uint32_t u = t; u <= cmask; u += 64) atomicAdd(pd + u, pb[k2_fpos(u)]);
+                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
+                for (uint32_t u = t; u <= cmask; u += (1u << TA)) atomicAdd(pd + u, pb[k2_fpos(u)]);
             }
         }
-        k2_bar_atom(half);  // the gather is done before the next setting's exchange stores
+        k2_bar_atom_g<TA>(half);  // the gather is done before the next setting's exchange stores
     }
     cp_async_wait0();
     tm_fence_before();
@@ -338,14 +390,14 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
         tm_dealloc(tmem_sm[0], k2ColsFwd);
     }
 }
-template <bool CACHE>
+template <bool CACHE, int C = 12>
 __global__ void __launch_bounds__(k2T, 3) k_forward_2r(const FwdArgs a) {
-    forward_2r_body<CACHE>(a, blockIdx.x);
+    forward_2r_body<CACHE, C>(a, blockIdx.x);
 }
-template <bool CACHE>
+template <bool CACHE, int C = 12>
 __global__ void __launch_bounds__(k2T, 3) k_forward_2r_multi(const FwdArgs *__restrict__ args, const int *__restrict__ start, int count) {
     const int i = multi_find(start, count, (int)blockIdx.x);
     const FwdArgs a = args[i];
-    forward_2r_body<CACHE>(a, (int)blockIdx.x - start[i]);
+    forward_2r_body<CACHE, C>(a, (int)blockIdx.x - start[i]);
 }
 

@@ -402,6 +402,50 @@ __device__ __forceinline__ void k2p_load_B(f2p (&X)[32], f2p (&Y)[32], const flo
     }
 }
 
+// Chunks of C = 10, 11 qubits (TA = C - 6 thread bits per atom, element i of
+// thread t at u = t + 2^TA i): atom a of the CTA keeps its planes' rows at
+// floats (a / 2^(6-TA)) k2pBuf + (a mod 2^(6-TA)) 68 2^TA (the imaginary plane
+// k2pPlane further, as for TA = 6), so the round-B row accesses, the scatter
+// positions k2p_pos(u) and the plane offset are unchanged.  Round A: element
+// i at row (2^TA i) / 64, column 2 t + c(i), c(i) = 2 ((2^TA i) mod 32) +
+// ((2^TA i) mod 64) / 32, a compile-time offset from 8 t.
+template <int TA>
+__host__ __device__ constexpr int k2p_atom_off(int ai) {
+    return (ai >> (6 - TA)) * k2pBuf + (ai & ((1 << (6 - TA)) - 1)) * (k2pPR << TA);
+}
+template <int TA>
+__host__ __device__ constexpr uint32_t k2p_offA(int e) {
+    return 4u * (uint32_t)(k2pPR * ((e << TA) >> 6) + 2 * ((e << TA) & 31) + (((e << TA) & 63) >> 5));
+}
+template <int TA>
+__device__ __forceinline__ void k2p_store_A_g(const f2p (&X)[32], const f2p (&Y)[32], float *wk, uint32_t t) {
+    const uint32_t bx = smem_u32(wk) + 8u * t, by = bx + 4u * k2pPlane;
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        k2p_st2(bx + k2p_offA<TA>(p), bx + k2p_offA<TA>(p + 32), X[p]);
+        k2p_st2(by + k2p_offA<TA>(p), by + k2p_offA<TA>(p + 32), Y[p]);
+    }
+}
+// Round A's elements, each position cleared behind its read.
+template <int TA>
+__device__ __forceinline__ void k2p_load_A_clear_g(f2p (&X)[32], f2p (&Y)[32], float *wk, uint32_t t) {
+    const uint32_t bx = smem_u32(wk) + 8u * t, by = bx + 4u * k2pPlane;
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        X[p] = k2p_ld2(bx + k2p_offA<TA>(p), bx + k2p_offA<TA>(p + 32));
+        Y[p] = k2p_ld2(by + k2p_offA<TA>(p), by + k2p_offA<TA>(p + 32));
+        k2p_st2(bx + k2p_offA<TA>(p), bx + k2p_offA<TA>(p + 32), 0ull);
+        k2p_st2(by + k2p_offA<TA>(p), by + k2p_offA<TA>(p + 32), 0ull);
+    }
+}
+// the last atom's imaginary rows end where the two 64-row atom buffers end
+template <int TA>
+__host__ __device__ constexpr bool k2p_atoms_tile() {
+    return k2p_atom_off<TA>((k2T >> TA) - 1) + k2pPlane + (k2pPR << TA) == 2 * k2pBuf &&
+           (k2pPR << TA) * (1 << (6 - TA)) == k2pPlane;
+}
+static_assert(k2p_atoms_tile<6>() && k2p_atoms_tile<5>() && k2p_atoms_tile<4>(), "atom planes tile the buffers");
+
 // Adjoint CTA = (bin, high pattern f, atom pair kp).  Per setting: round A,
 // exchange, round B, the c multiply, inverse round B, exchange, inverse round
 // A, and z += v in TMEM (round A's layout).  Two block barriers per setting,
@@ -629,16 +673,19 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-template <int k2cStage>
+// C < 12: 2^(13-C) atoms per CTA; each stages 2 k2cStage / 2^(13-C)
+// entries per setting (the same shared memory in all).
+template <int k2cStage, int C = 12>
 __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
+    constexpr int TA = C - 6, APC = k2T >> TA, SA = 2 * k2cStage / APC;  // per-atom staged entries
     constexpr K2cSmem sp = k2c_smem(k2cStage);
     extern __shared__ __align__(16) unsigned char smem[];
     uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
-    const int KP = (a.K + 1) >> 1;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & ((1u << TA) - 1u), half = tid >> TA;
+    const int KP = (a.K + APC - 1) / APC;
     const int unit = cta;
     const int kp = unit % KP;
     const int rest = unit / KP;
@@ -647,14 +694,15 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
     if (bin >= *a.n_bins) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
-    const int k = 2 * kp + (int)half;
+    const int k = APC * kp + (int)half;
     const bool active = k < a.K;
-    float *wk = reinterpret_cast<float *>(smem + sp.work) + half * k2pBuf;
-    float2 *stp = reinterpret_cast<float2 *>(smem + sp.stage_p) + half * 2 * k2cStage;
-    uint32_t *stu = reinterpret_cast<uint32_t *>(smem + sp.stage_u) + half * 2 * k2cStage;
-    float *stc = reinterpret_cast<float *>(smem + sp.stage_c) + half * 2 * k2cStage;
-    const uint32_t lo = k2p_lo(t), colA = k2p_col(lo);
-    constexpr uint32_t cmask = 4095u;
+    float *wk = reinterpret_cast<float *>(smem + sp.work) + k2p_atom_off<TA>((int)half);
+    float2 *stp = reinterpret_cast<float2 *>(smem + sp.stage_p) + half * 2 * SA;
+    uint32_t *stu = reinterpret_cast<uint32_t *>(smem + sp.stage_u) + half * 2 * SA;
+    float *stc = reinterpret_cast<float *>(smem + sp.stage_c) + half * 2 * SA;
+    // round A: TA = 6 permutes the columns among the threads (conflict-free stores)
+    const uint32_t lo = TA == 6 ? k2p_lo(t) : t, colA = k2p_col(lo);
+    constexpr uint32_t cmask = (1u << C) - 1u;
     if (warp == 0) tm_alloc(tmem_sm, k2cCols);
     for (int u = tid; u < 2 * k2pBuf; u += k2T) reinterpret_cast<float *>(smem + sp.work)[u] = 0.f;
     fx_stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, masks_sm, meta_sm);
@@ -672,13 +720,18 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
         for (int q = 0; q < 4; ++q) k2p_tm_st16(t_z + 32u * q, zero);
     }
     f2p X[32], Y[32];
-    if (active) {
+    // The TMEM accesses (.sync.aligned) need whole warps: atoms of 16 threads
+    // share a warp, so there an inactive atom (k >= K) runs the loop too, on
+    // atom 0's entries in its own planes (cleared behind every setting), and
+    // only its z write is skipped.  Larger atoms are whole warps.
+    const bool run = TA >= 5 ? active : true;
+    if (run) {
         auto issue = [&](int si) {
             if (si < bcount) {
                 const SetMeta mt = meta_sm[si];
-                const int nst = mt.cnt < k2cStage ? mt.cnt : k2cStage;
-                const int o = (si & 1) * k2cStage;
-                for (int j = t; j < nst; j += 64) {
+                const int nst = mt.cnt < SA ? mt.cnt : SA;
+                const int o = (si & 1) * SA;
+                for (int j = t; j < nst; j += (1 << TA)) {
                     cp_async4(stu + o + j, outcome + mt.lo + j);
                     cp_async4(stc + o + j, c_obs + mt.lo + j);
                     cp_async8(stp + o + j, phk + mt.lo + j);
@@ -693,9 +746,9 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
             cp_async_wait0();  // this thread's entries of setting si have landed
             issue(si + 1);     // into the buffer this thread read for setting si - 1
             {
-                const int o = (si & 1) * k2cStage;
-                for (int j = t; j < mt.cnt; j += 64) {
-                    const bool st = j < k2cStage;
+                const int o = (si & 1) * SA;
+                for (int j = t; j < mt.cnt; j += (1 << TA)) {
+                    const bool st = j < SA;
                     const uint32_t u = (st ? stu[o + j] : outcome[mt.lo + j]) & cmask;
                     const float cy = (st ? stc[o + j] : c_obs[mt.lo + j]) * mt.cs;
                     const float2 ph = st ? stp[o + j] : phk[mt.lo + j];
@@ -704,42 +757,45 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
                     wk[k2pPlane + pos] = cy * ph.y;
                 }
             }
-            k2_bar_atom(half);  // the scatter is visible
+            k2_bar_atom_g<TA>(half);  // the scatter is visible
             k2p_load_B(X, Y, wk, t);
             // the inverse rounds (the Hermitian chunk factors are their own
             // conjugate transposes): round B, then round A
 #pragma unroll 1
             for (int ph = 0; ph < 2; ++ph) {
-                const uint32_t sh = ph ? 6u : 0u;
-                butterfly_herm_p(X, Y, (mk.x >> sh) & 63u, (mk.y >> sh) & 63u);
+                butterfly_herm_p(X, Y, ph ? k2_maskA<TA>(mk.x) : (mk.x & 63u), ph ? k2_maskA<TA>(mk.y) : (mk.y & 63u));
                 if (ph == 0) {
                     k2p_store_B(X, Y, wk, t);
-                    k2_bar_atom(half);
-                    k2p_load_A(X, Y, wk, colA);
-                    const uint32_t bx = smem_u32(wk + colA), by = bx + 4u * k2pPlane;
+                    k2_bar_atom_g<TA>(half);
+                    if constexpr (TA == 6) {
+                        k2p_load_A(X, Y, wk, colA);
+                        const uint32_t bx = smem_u32(wk + colA), by = bx + 4u * k2pPlane;
 #pragma unroll
-                    for (int p = 0; p < 32; ++p) {
-                        k2p_st2(bx + 4u * k2pPR * p, bx + 4u * k2pPR * (p + 32), 0ull);
-                        k2p_st2(by + 4u * k2pPR * p, by + 4u * k2pPR * (p + 32), 0ull);
+                        for (int p = 0; p < 32; ++p) {
+                            k2p_st2(bx + 4u * k2pPR * p, bx + 4u * k2pPR * (p + 32), 0ull);
+                            k2p_st2(by + 4u * k2pPR * p, by + 4u * k2pPR * (p + 32), 0ull);
+                        }
+                    } else {
+                        k2p_load_A_clear_g<TA>(X, Y, wk, t);
                     }
                 }
             }
             k2p_tm_acc(t_z, X, Y);
-            k2_bar_atom(half);  // every position is zero again before the next scatter
+            k2_bar_atom_g<TA>(half);  // every position is zero again before the next scatter
         }
         cp_async_wait0();
     }
     tm_wait_st();
+    if (run) k2p_tm_ld(t_z, X, Y);
     if (active) {
-        k2p_tm_ld(t_z, X, Y);
-        float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << 12) + lo;
+        float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << C) + lo;
 #pragma unroll
         for (int p = 0; p < 32; ++p) {
             float xa, xb, ya, yb;
             p_unpack(X[p], xa, xb);
             p_unpack(Y[p], ya, yb);
-            zo[64u * p] = make_float2(xa, ya);
-            zo[64u * (p + 32)] = make_float2(xb, yb);
+            zo[(uint32_t)p << TA] = make_float2(xa, ya);
+            zo[(uint32_t)(p + 32) << TA] = make_float2(xb, yb);
         }
     }
     tm_fence_before();
@@ -749,11 +805,13 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
         tm_dealloc(tmem_sm[0], k2cCols);
     }
 }
+template <int C = 12>
 __global__ void __launch_bounds__(k2T, 3) k_adjoint_2c(const AdjArgs a) {
-    adjoint_2c_body<k2cStageSingle>(a, blockIdx.x);
+    adjoint_2c_body<k2cStageSingle, C>(a, blockIdx.x);
 }
+template <int C = 12>
 __global__ void __launch_bounds__(k2T, 2) k_adjoint_2c_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
     const int i = multi_find(start, count, (int)blockIdx.x);
     const AdjArgs a = args[i];
-    adjoint_2c_body<k2cStageMulti>(a, (int)blockIdx.x - start[i]);
+    adjoint_2c_body<k2cStageMulti, C>(a, (int)blockIdx.x - start[i]);
 }
