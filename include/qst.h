@@ -72,9 +72,7 @@ typedef struct qst_params {
                              runs 1); 1 = three rounds of four qubits on fixed qubit groups, 16
                              amplitudes per thread (compile-time shared-memory offsets, warp-local
                              middle exchange).  Whole states of 10, 11 qubits: 2 = the same two
-                             rounds with 2^(n-6) threads per atom (2^(13-n) atoms per CTA); their
-                             adjoint works from the forward's transforms (the plan always holds
-                             the K x nnz buffer; qst_adjoint recomputes them with the forward).
+                             rounds with 2^(n-6) threads per atom (2^(13-n) atoms per CTA).
                              States of 5..9 qubits held in one chunk: 3 = one
                              warp per (bin, atom), 2^(n-5) amplitudes per lane, the low five bits'
                              butterflies by lane shuffles (QST_ERR_UNSUPPORTED for other plans).
@@ -83,9 +81,9 @@ typedef struct qst_params {
                              atom), each CTA two 12-qubit rows in two rounds of six qubits, then a
                              round of the top four chunk qubits over the cluster (asking for 4
                              selects these chunks; they take no other value).  -1 = automatic: 3
-                             for whole states of 5..9 qubits, 4 for 16-qubit chunks, for whole
-                             states of 10, 11 qubits 2 when nnz <= M 2^n / 4 else 0, for 12-qubit
-                             chunks 2 when a work bin may hold >= 32 settings, else 1.  Other
+                             for whole states of 5..9 qubits, 4 for 16-qubit chunks, 2 for whole
+                             states of 10, 11 qubits, for 12-qubit chunks 2 when a work bin may
+                             hold >= 32 settings, else 1.  Other
                              values: QST_ERR_INVALID_ARG.  Default -1. */
     int phi_cache;        /* qst_evaluate's transform cache: the forward stores the transform of every
                              atom at every observed outcome (K x nnz complex64, owned by the plan) and
@@ -93,9 +91,11 @@ typedef struct qst_params {
                              skips the high-bit pass before them).  Two-round plans, the n = 20
                              path (12-qubit chunks) and 16-qubit chunks.  1 = on
                              (QST_ERR_UNSUPPORTED for other plans), 0 = off, -1 = automatic: on for
-                             two-round plans when K x nnz x 8 bytes <= 16 GiB and for 16-qubit
-                             chunks, off on the n = 20 path (whose adjoint recomputes the rotated
-                             amplitudes unless asked).  qst_forward and qst_adjoint never use it
+                             two-round plans when K x nnz x 8 bytes <= 16 GiB (for whole states of
+                             10, 11 qubits only when nnz <= M 2^n / 4: with denser outcomes the
+                             cache costs more than recomputing) and for 16-qubit chunks, off on the
+                             n = 20 path (whose adjoint recomputes the rotated amplitudes unless
+                             asked).  qst_forward and qst_adjoint never use it
                              (16-qubit chunks: their adjoint kernel reads transforms, and
                              qst_adjoint first recomputes them with the forward kernel into the
                              plan's buffer, which those plans always hold).  Default -1. */

@@ -1390,7 +1390,11 @@ void launch_adjoint_units(qst_plan p, const AdjArgs &a0, int units, cudaStream_t
         return;
     }
     if (p->fx2) {
-        k_adjoint_2r<<<units * ((p->K + 1) / 2), k2T, k2p_smem().total, st>>>(a);
+        const int grid = units * k2_atom_groups(p->K, p->c);
+        with_chunk2(p->c, [&](auto cc) {
+            constexpr int C = decltype(cc)::value;
+            k_adjoint_2r<C><<<grid, k2T, k2p_smem().total, st>>>(a);
+        });
         return;
     }
     const int grid = units * p->K;
@@ -1636,14 +1640,12 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // bin measured ~20 % faster with three rounds).  The wide path's units hold
     // one setting each: it always runs the three-round kernels (264 against
     // 356 ms on the n = 20 workload).
-    // Whole states of 10, 11 qubits: the two-round kernels (their adjoint reads
-    // the forward's transforms, 8 bytes per observed entry and atom) when at most
-    // a quarter of the outcomes are observed, else the per-setting-round kernels:
-    // n = 11, M = 2000, K = 8 took 0.349 against 0.412 ms per evaluation at 200
-    // shots a setting, 1.07 against 0.71 ms at 5000 (about 1800 of 2048 observed).
+    // Whole states of 10, 11 qubits run the two-round kernels; their transform
+    // cache (8 bytes per observed entry and atom) pays only when at most a quarter
+    // of the outcomes are observed, so qst_evaluate's adjoint reads it there and
+    // recomputes otherwise (phi_cache -1).
     const bool sparse = (int64_t)nnz * 4 <= ((int64_t)M << c);
-    const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds
-                                         : (c < 12 && r == 0 && c >= 10 ? (sparse ? 2 : 0) : (p->smax >= 32 ? 2 : 1));
+    const int fr = prm.fixed_rounds >= 0 ? prm.fixed_rounds : (c < 12 && r == 0 && c >= 10 ? 2 : (p->smax >= 32 ? 2 : 1));
     // the cluster kernels are the 16-qubit chunks' only kernels (fixed_rounds 4, or automatic)
     if (cl != (prm.fixed_rounds == 4 || (cl && prm.fixed_rounds == -1))) {
         delete p;
@@ -1728,14 +1730,14 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     // (on the wide path with 12-qubit chunks, n = 20, only when asked for: there the adjoint
     // recomputes by default)
     if (!rc && nnz > 0 &&
-        ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30)))) ||
-         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0) || cl || (p->fx2 && c < 12)))
+        ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30) &&
+                                            (c == 12 || sparse)))) ||
+         (wide && p->fx && prm.phi_cache == 1) || (p->fx2 && prm.precision > 0) || cl))
         rc = dalloc(p, &p->phi, (size_t)K * nnz);
     // with precision > 0 the buffer is also the tensor-core adjoint's input when the cache is off
     // (the cluster kernels' adjoint always reads transforms: without the cache it recomputes them
     // into the same buffer first)
-    // (the same for the two-round kernels of 10- and 11-qubit chunks, which have no recomputing adjoint)
-    p->cache_on = p->phi && !((prm.precision > 0 || cl || (p->fx2 && c < 12)) && prm.phi_cache == 0);
+    p->cache_on = p->phi && !((prm.precision > 0 || cl) && prm.phi_cache == 0);
     if (!rc && prm.precision > 0) {
         rc = dalloc(p, &p->tc_ops, (size_t)kTcOps * kTcOpBytes);
         if (!rc) {
@@ -1782,7 +1784,9 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
             cudaFuncSetAttribute(k_forward_2r<true, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
             cudaFuncSetAttribute(k_forward_2r<false, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
             cudaFuncSetAttribute(k_forward_2r<true, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
-            cudaFuncSetAttribute(k_adjoint_2r, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+            cudaFuncSetAttribute(k_adjoint_2r<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+            cudaFuncSetAttribute(k_adjoint_2r<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+            cudaFuncSetAttribute(k_adjoint_2r<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
         }
         if (prm.precision > 0) {
             cudaFuncSetAttribute(k_forward_tc<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemAlloc);
@@ -2008,7 +2012,7 @@ qst_status adjoint_core(qst_plan p, const float *psi, const float *w, const int6
         return launch(p, QST_KERNEL_HSUM, st, [&] { k_hsum<<<p->K, 256, 0, st>>>(p->hdot, p->c, invBw, grad_w, nullptr); });
     }
     const int units = p->nb_max << p->r;
-    if (((p->fx2 && (p->prm.precision > 0 || p->c < 12)) || p->cl) && !phi_cache) {
+    if (((p->fx2 && p->prm.precision > 0) || p->cl) && !phi_cache) {
         // the tensor-core and cluster adjoints read transforms: recompute them with the plan's
         // forward (its w |.|^2 partials go to the plan's scratch and are not read)
         FwdArgs f;
@@ -3037,11 +3041,11 @@ __global__ void __launch_bounds__(256) k_hsum_multi(const HsumArgs *__restrict__
 // Chunk-kernel family of a plan: the multi-instance forward / adjoint
 // launches group instances by it (same kernel, block and shared memory).
 // >= 0: generic kernels, 100 c + A; -10 - n: warp-unit kernels of n qubits
-enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3, kFam2rCache11 = -4, kFam2rCache10 = -5 };
+enum { kFam2rCache = -1, kFam2r = -2, kFamFx = -3, kFam2rCache11 = -4, kFam2rCache10 = -5, kFam2r11 = -6, kFam2r10 = -7 };
 int plan_family(const qst_plan_s *p) {
     if (p->fw) return -10 - p->n;
-    if (p->fx2 && p->c == 11) return kFam2rCache11;  // (such plans join a batch's launches with their cache on)
-    if (p->fx2 && p->c == 10) return kFam2rCache10;
+    if (p->fx2 && p->c == 11) return p->cache_on ? kFam2rCache11 : kFam2r11;
+    if (p->fx2 && p->c == 10) return p->cache_on ? kFam2rCache10 : kFam2r10;
     if (p->fx2) return p->cache_on ? kFam2rCache : kFam2r;
     if (p->fx) return kFamFx;
     return 100 * p->c + p->A;
@@ -3108,13 +3112,19 @@ void set_family_attrs(int fam) {
         cudaFuncSetAttribute(k_forward_2r_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_forward_2r_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_adjoint_2c_multi<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
-        cudaFuncSetAttribute(k_adjoint_2r_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+        cudaFuncSetAttribute(k_adjoint_2r_multi<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
     } else if (fam == kFam2rCache11) {
         cudaFuncSetAttribute(k_forward_2r_multi<true, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_adjoint_2c_multi<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
     } else if (fam == kFam2rCache10) {
         cudaFuncSetAttribute(k_forward_2r_multi<true, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
         cudaFuncSetAttribute(k_adjoint_2c_multi<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2c_smem(k2cStageMulti).total);
+    } else if (fam == kFam2r11) {
+        cudaFuncSetAttribute(k_forward_2r_multi<false, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+        cudaFuncSetAttribute(k_adjoint_2r_multi<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
+    } else if (fam == kFam2r10) {
+        cudaFuncSetAttribute(k_forward_2r_multi<false, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_smem_fwd().total);
+        cudaFuncSetAttribute(k_adjoint_2r_multi<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2p_smem().total);
     } else if (fam <= -15) {
         // at most 16 KB of shared memory: no attribute
     } else if (fam == kFamFx) {
@@ -3165,7 +3175,7 @@ qst_status batch_create(qst_batch *out, int count, const int *n, const int *M, c
     // multi-instance launches for every plan off the wide path and off the tensor cores
     b->multi = true;
     for (auto p : b->plans)
-        if (p->wide || p->cl || p->prm.precision > 0 || (p->fx2 && p->c < 12 && !p->cache_on)) b->multi = false;
+        if (p->wide || p->cl || p->prm.precision > 0) b->multi = false;
     if (b->multi) {
         for (auto p : b->plans) set_family_attrs(plan_family(p));
         if (cudaGetLastError() != cudaSuccess) {
@@ -3405,6 +3415,8 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
             else if (fam == kFam2r) k_forward_2r_multi<false><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFam2rCache11) k_forward_2r_multi<true, 11><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFam2rCache10) k_forward_2r_multi<true, 10><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r11) k_forward_2r_multi<false, 11><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r10) k_forward_2r_multi<false, 10><<<grid, k2T, k2_smem_fwd().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_forward_fx_multi<<<grid, kFxT, fx_smem(false).total, st>>>(a, start, cnt);
             else if (fam <= -15)
                 with_wu(-10 - fam, [&](auto nb) {
@@ -3423,7 +3435,9 @@ void batch_launch(qst_batch b, const BatchLaunch &L, cudaStream_t st) {
             if (fam == kFam2rCache) k_adjoint_2c_multi<12><<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
             else if (fam == kFam2rCache11) k_adjoint_2c_multi<11><<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
             else if (fam == kFam2rCache10) k_adjoint_2c_multi<10><<<grid, k2T, k2c_smem(k2cStageMulti).total, st>>>(a, start, cnt);
-            else if (fam == kFam2r) k_adjoint_2r_multi<<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r) k_adjoint_2r_multi<12><<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r11) k_adjoint_2r_multi<11><<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
+            else if (fam == kFam2r10) k_adjoint_2r_multi<10><<<grid, k2T, k2p_smem().total, st>>>(a, start, cnt);
             else if (fam == kFamFx) k_adjoint_fx_multi<<<grid, kFxT, fx_smem(true).total, st>>>(a, start, cnt);
             else if (fam <= -15)
                 with_wu(-10 - fam, [&](auto nb) {

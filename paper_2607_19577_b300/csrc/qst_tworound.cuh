@@ -311,6 +311,10 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
     };
     const float wkk = active ? a.w[k] : 0.f;
     float *pk = a.ppart + (size_t)(active ? k : 0) * a.nnz;
+    // the CTA's atoms' weights (the small-atom gather serves every atom)
+    float wsm[TA < 6 ? APC : 1];
+#pragma unroll
+    for (int aa = 0; aa < (TA < 6 ? APC : 1); ++aa) wsm[aa] = APC * kp + aa < a.K ? a.w[APC * kp + aa] : 0.f;
     issue(0);
     k2_build_source<C>(t_src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)(active ? k : 0) * D, active, f,
                        b.xytop, b.ytop, t);
@@ -353,6 +357,44 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
         // which every thread finished before the barrier above
         issue(si + 1);
         const uint32_t *st = stage + (si & 1) * k2Stage;
+        if constexpr (TA < 6) {
+            // Small atoms (2^TA threads) would each walk the setting's whole
+            // outcome list; instead every thread reads an outcome once and
+            // serves all of the CTA's atoms (block barriers around the gather).
+            float2 *W = reinterpret_cast<float2 *>(smem + sp.work);
+            for (int j = tid; j < mt.cnt; j += k2T) {
+                const uint32_t u = (j < k2Stage ? st[j] : outcome[mt.lo + j]) & cmask;
+#pragma unroll
+                for (int aa = 0; aa < APC; ++aa) {
+                    const int ka = APC * kp + aa;
+                    if (ka >= a.K) break;
+                    const float2 *wa = W + aa * (k2Row << TA);
+                    float *pa = a.ppart + (size_t)ka * a.nnz;
+                    if (CACHE) {
+                        const float2 ph = wa[k2Row * (u >> 6) + (u & 63u)];
+                        pa[mt.lo + j] = scaled_abs2(wsm[aa] * mt.cs, ph);
+                        a.phi_obs[(size_t)ka * a.nnz + mt.lo + j] = ph;
+                    } else {
+                        pa[mt.lo + j] = reinterpret_cast<const float *>(wa)[k2_fpos(u)];
+                    }
+                }
+            }
+            if (a.p_dense) {
+                const int s = a.order[b.start + si];
+                float *pd = a.p_dense + (size_t)s * D + ((size_t)f << C);
+                for (uint32_t u = tid; u <= cmask; u += k2T) {
+#pragma unroll
+                    for (int aa = 0; aa < APC; ++aa) {
+                        if (APC * kp + aa >= a.K) break;
+                        const float2 *wa = W + aa * (k2Row << TA);
+                        atomicAdd(pd + u, CACHE ? scaled_abs2(wsm[aa] * mt.cs, wa[k2Row * (u >> 6) + (u & 63u)])
+                                                : reinterpret_cast<const float *>(wa)[k2_fpos(u)]);
+                    }
+                }
+            }
+            __syncthreads();  // the gather is done before the next setting's exchange stores
+            continue;
+        }
         if (active && CACHE) {
             float2 *phk = a.phi_obs + (size_t)k * a.nnz;
             for (int j = t; j < mt.cnt; j += (1 << TA)) {

@@ -243,15 +243,17 @@ __device__ __forceinline__ void k2p_tm_acc(uint32_t taddr, const f2p (&X)[32], c
 // Chunk f of (U_h (x) I) psi_k in round A's layout (element i of thread t =
 // amplitude lo(t) + 64 i) -> TMEM columns 0..127 in the packed order, built
 // for elements 8Q..8Q+7 and 32+8Q..32+8Q+7 (16 X and 16 Y columns) at a time.
-// An inactive atom (k >= K) gets zeros.
+// An inactive atom (k >= K) gets zeros.  C < 12: element i of thread lo is
+// amplitude lo + 2^(C-6) i.
+template <int C = 12>
 __device__ __forceinline__ void k2p_build_source(uint32_t t_src, const float2 *psik, bool active, uint32_t f,
                                                 uint32_t xytop, uint32_t ytop, uint32_t lo) {
     float2 acc[64];
 #define QST_K2_PART(Q)                                                                                   \
     {                                                                                                    \
         if (active) {                                                                                    \
-            build_source_regs<12, 6, 8 * (Q), 8>(acc, psik, f, xytop, ytop, lo);                         \
-            build_source_regs<12, 6, 32 + 8 * (Q), 8>(acc, psik, f, xytop, ytop, lo);                    \
+            build_source_regs<C, 6, 8 * (Q), 8>(acc, psik, f, xytop, ytop, lo);                          \
+            build_source_regs<C, 6, 32 + 8 * (Q), 8>(acc, psik, f, xytop, ytop, lo);                     \
         } else {                                                                                         \
             _Pragma("unroll") for (int i = 0; i < 8; ++i) {                                              \
                 acc[8 * (Q) + i] = make_float2(0.f, 0.f);                                                \
@@ -426,6 +428,15 @@ __device__ __forceinline__ void k2p_store_A_g(const f2p (&X)[32], const f2p (&Y)
         k2p_st2(by + k2p_offA<TA>(p), by + k2p_offA<TA>(p + 32), Y[p]);
     }
 }
+template <int TA>
+__device__ __forceinline__ void k2p_load_A_g(f2p (&X)[32], f2p (&Y)[32], const float *wk, uint32_t t) {
+    const uint32_t bx = smem_u32(wk) + 8u * t, by = bx + 4u * k2pPlane;
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        X[p] = k2p_ld2(bx + k2p_offA<TA>(p), bx + k2p_offA<TA>(p + 32));
+        Y[p] = k2p_ld2(by + k2p_offA<TA>(p), by + k2p_offA<TA>(p + 32));
+    }
+}
 // Round A's elements, each position cleared behind its read.
 template <int TA>
 __device__ __forceinline__ void k2p_load_A_clear_g(f2p (&X)[32], f2p (&Y)[32], float *wk, uint32_t t) {
@@ -457,8 +468,13 @@ static_assert(k2p_atoms_tile<6>() && k2p_atoms_tile<5>() && k2p_atoms_tile<4>(),
 //     first barrier, and which setting si + 1 reads after its first barrier.
 // A thread's round-A (round-B) exchange addresses are the same in both
 // directions, so it only overwrites addresses that it has read itself.
+// C < 12: 2^(13-C) atoms per CTA (round A's layout and the atoms' plane
+// offsets as in the cached adjoint below); the dense c buffers are shared by
+// all of them, as by the two atoms of C = 12.
+template <int C = 12>
 __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) {
     if (a.skip && *a.skip) return;
+    constexpr int TA = C - 6, APC = k2T >> TA;
     constexpr K2Smem sp = k2p_smem();
     extern __shared__ __align__(16) unsigned char smem[];
     float *cbuf = reinterpret_cast<float *>(smem + sp.fbuf);
@@ -467,8 +483,8 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
     uint2 *masks_sm = reinterpret_cast<uint2 *>(smem + sp.masks);
     SetMeta *meta_sm = reinterpret_cast<SetMeta *>(smem + sp.meta);
     uint32_t *tmem_sm = reinterpret_cast<uint32_t *>(smem + sp.tmem);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & 63u, half = tid >> 6;
-    const int KP = (a.K + 1) >> 1;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, t = tid & ((1u << TA) - 1u), half = tid >> TA;
+    const int KP = (a.K + APC - 1) / APC;
     const int unit = cta;
     const int kp = unit % KP;
     const int rest = unit / KP;
@@ -477,11 +493,11 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
     if (bin >= *a.n_bins) return;
     const Bin b = a.bins[bin];
     const int D = 1 << a.n;
-    const int k = 2 * kp + (int)half;
+    const int k = APC * kp + (int)half;
     const bool active = k < a.K;
-    float *wk = reinterpret_cast<float *>(smem + sp.work) + half * k2pBuf;
-    const uint32_t lo = k2p_lo(t), colA = k2p_col(lo);
-    constexpr uint32_t cmask = 4095u;
+    float *wk = reinterpret_cast<float *>(smem + sp.work) + k2p_atom_off<TA>((int)half);
+    const uint32_t lo = TA == 6 ? k2p_lo(t) : t, colA = k2p_col(lo);
+    constexpr uint32_t cmask = (1u << C) - 1u;
     if (warp == 0) tm_alloc(tmem_sm, k2ColsAdj);
     for (int u = tid; u < 2 * k2pPlane; u += k2T) cbuf[u] = 0.f;
     fx_stage_bin(b, f, (1 << a.r) + 1, a.order, a.plans, a.row_ptr, a.choff, masks_sm, meta_sm);
@@ -520,8 +536,8 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
         }
     };
     issue(0);
-    k2p_build_source(t_src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)(active ? k : 0) * D, active, f, b.xytop,
-                    b.ytop, lo);
+    k2p_build_source<C>(t_src, a.psi + (size_t)bin * a.src_bin_stride + (size_t)(active ? k : 0) * D, active, f,
+                        b.xytop, b.ytop, lo);
     {
         const uint32_t zero[32] = {};
         tm_st(t_z, zero);
@@ -542,10 +558,11 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
         // exchange A -> B, the c multiply, the exchange B -> A
 #pragma unroll 1
         for (int ph = 0; ph < 4; ++ph) {
-            const uint32_t sh = (ph == 0 || ph == 3) ? 6u : 0u;
-            butterfly_herm_p(X, Y, (mk.x >> sh) & 63u, (mk.y >> sh) & 63u);
+            const bool rA = ph == 0 || ph == 3;
+            butterfly_herm_p(X, Y, rA ? k2_maskA<TA>(mk.x) : (mk.x & 63u), rA ? k2_maskA<TA>(mk.y) : (mk.y & 63u));
             if (ph == 0) {
-                k2p_store_A(X, Y, wk, colA);
+                if constexpr (TA == 6) k2p_store_A(X, Y, wk, colA);
+                else k2p_store_A_g<TA>(X, Y, wk, t);
                 __syncthreads();
                 k2p_load_B(X, Y, wk, t);
             } else if (ph == 1) {
@@ -562,7 +579,8 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
             } else if (ph == 2) {
                 k2p_store_B(X, Y, wk, t);
                 __syncthreads();
-                k2p_load_A(X, Y, wk, colA);
+                if constexpr (TA == 6) k2p_load_A(X, Y, wk, colA);
+                else k2p_load_A_g<TA>(X, Y, wk, t);
             }
         }
         k2p_tm_acc(t_z, X, Y);
@@ -573,16 +591,16 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
     }
     cp_async_wait0();
     tm_wait_st();
+    k2p_tm_ld(t_z, X, Y);  // every warp whole (.sync.aligned: 16-thread atoms share warps)
     if (active) {
-        k2p_tm_ld(t_z, X, Y);
-        float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << 12) + lo;
+        float2 *zo = a.zbuf + ((size_t)bin * a.K + k) * D + ((size_t)f << C) + lo;
 #pragma unroll
         for (int p = 0; p < 32; ++p) {
             float xa, xb, ya, yb;
             p_unpack(X[p], xa, xb);
             p_unpack(Y[p], ya, yb);
-            zo[64u * p] = make_float2(xa, ya);
-            zo[64u * (p + 32)] = make_float2(xb, yb);
+            zo[(uint32_t)p << TA] = make_float2(xa, ya);
+            zo[(uint32_t)(p + 32) << TA] = make_float2(xb, yb);
         }
     }
     tm_fence_before();
@@ -592,13 +610,15 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
         tm_dealloc(tmem_sm[0], k2ColsAdj);
     }
 }
+template <int C = 12>
 __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r(const AdjArgs a) {
-    adjoint_2r_body(a, blockIdx.x);
+    adjoint_2r_body<C>(a, blockIdx.x);
 }
+template <int C = 12>
 __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r_multi(const AdjArgs *__restrict__ args, const int *__restrict__ start, int count) {
     const int i = multi_find(start, count, (int)blockIdx.x);
     const AdjArgs a = args[i];
-    adjoint_2r_body(a, (int)blockIdx.x - start[i]);
+    adjoint_2r_body<C>(a, (int)blockIdx.x - start[i]);
 }
 
 // Cached adjoint (the evaluate path): the forward kernel has stored the chunk

@@ -291,26 +291,27 @@ def test_parity_two_round_bins_and_atoms(n, M, K, smax, seed):
             dense=dense)
 
 
-@pytest.mark.parametrize("n,M,K,smax,seed", [(11, 23, 3, 96, 0), (11, 37, 4, 5, 1), (11, 19, 9, 1, 2),
-                                              (10, 29, 5, 96, 3), (10, 33, 8, 7, 4), (10, 21, 11, 2, 5)])
-def test_parity_two_round_small_chunks(n, M, K, smax, seed):
+@pytest.mark.parametrize("n,M,K,smax,shots,seed", [(11, 23, 3, 96, 1500, 0), (11, 37, 4, 5, 300, 1),
+                                                    (11, 19, 9, 1, 1500, 2), (10, 29, 5, 96, 1500, 3),
+                                                    (10, 33, 8, 7, 150, 4), (10, 21, 11, 2, 1500, 5)])
+def test_parity_two_round_small_chunks(n, M, K, smax, shots, seed):
     """Whole states of 10 and 11 qubits on the two-round kernels (8 and 4 atoms
-    per CTA, atoms past K inactive; the adjoint always works from the forward's
-    transforms): qst_forward + qst_adjoint (the adjoint recomputes them) and
-    qst_evaluate (it reuses them) against the oracle, dense p, and bitwise equal."""
-    inst = synth.random_instance(n, M, K, 1500, 1300 + seed)
-    geo = qst.Plan(n, M, K, inst.nnz, fixed_rounds=2, max_bin_settings=smax).geometry()
+    per CTA, atoms past K inactive): qst_forward + qst_adjoint (the recomputing
+    adjoint), qst_evaluate with the transform cache (the cached adjoint) and with
+    the automatic choice (cache only for sparse outcomes) against the oracle,
+    dense p, and bitwise equal."""
+    inst = synth.random_instance(n, M, K, shots, 1300 + seed)
+    geo = qst.Plan(n, M, K, inst.nnz, max_bin_settings=smax).geometry()
     assert geo == {"chunk_qubits": n, "high_qubits": 0, "fixed_rounds": 2}
     ref = run_oracle(inst, dense=True)
-    sep = run_gpu(inst, dense=True, fixed_rounds=2, max_bin_settings=smax)
+    sep = run_gpu(inst, dense=True, max_bin_settings=smax)
     compare(inst, sep, ref, dense=True)
-    ev = run_gpu_evaluate(inst, fixed_rounds=2, max_bin_settings=smax)
+    ev = run_gpu_evaluate(inst, max_bin_settings=smax, phi_cache=1)
     compare(inst, ev, ref)
-    for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
-        assert np.array_equal(ev[key], sep[key]), key
-    off = run_gpu_evaluate(inst, fixed_rounds=2, max_bin_settings=smax, phi_cache=0)
-    for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
-        assert np.array_equal(off[key], sep[key]), key
+    auto = run_gpu_evaluate(inst, max_bin_settings=smax)
+    for other in (ev, auto):
+        for key in ["p_obs", "c_obs", "grad_psi", "grad_w"]:
+            assert np.array_equal(other[key], sep[key]), key
 
 
 @pytest.mark.parametrize("n,M,K,seed", [(5, 14, 3, 0), (12, 20, 4, 1), (16, 6, 2, 2)])
