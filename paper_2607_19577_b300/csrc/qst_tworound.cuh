@@ -222,12 +222,6 @@ __device__ __forceinline__ void k2_store_A_g(const float2 (&v)[64], float2 *wk, 
         for (int i = 0; i < 64; ++i) wk[k2Row * ((i << TA) >> 6) + ((i << TA) & 63) + t] = v[i];
     }
 }
-// Round A's butterflies act on chunk bits 6..C-1: register bits 6-TA..5 of
-// the element index (bits TA..5 are round B's).
-template <int TA>
-__device__ __forceinline__ uint32_t k2_maskA(uint32_t mask) {
-    return ((mask >> TA) & 63u) & ~((1u << (6 - TA)) - 1u);
-}
 // Barrier of one atom's 2^TA threads: a named barrier of 64 (TA = 6), else
 // the atom's lanes of its warp (TA <= 5: an atom lies inside one warp, and
 // an inactive atom's lanes may skip the loop that waits here).
@@ -328,7 +322,9 @@ __device__ __forceinline__ void forward_2r_body(const FwdArgs a, const int cta) 
         // round unrolled twice does not fit the instruction cache
 #pragma unroll 1
         for (int R = 0; R < 2; ++R) {
-            butterfly_herm<6>(v, R ? (mk.x & 63u) : k2_maskA<TA>(mk.x), R ? (mk.y & 63u) : k2_maskA<TA>(mk.y));
+            // round A: chunk bits 6..C-1 (its register bits 6-TA..5), round B: bits 0..5
+            const uint32_t sh = R ? 0u : (uint32_t)TA, keep = R ? 63u : 63u & ~((1u << (6 - TA)) - 1u);
+            butterfly_herm<6>(v, (mk.x >> sh) & keep, (mk.y >> sh) & keep);
             if (R == 0) {
                 k2_store_A_g<TA>(v, wk, t);
                 k2_bar_atom_g<TA>(half);

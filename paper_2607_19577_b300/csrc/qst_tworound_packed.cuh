@@ -558,8 +558,9 @@ __device__ __forceinline__ void adjoint_2r_body(const AdjArgs a, const int cta) 
         // exchange A -> B, the c multiply, the exchange B -> A
 #pragma unroll 1
         for (int ph = 0; ph < 4; ++ph) {
-            const bool rA = ph == 0 || ph == 3;
-            butterfly_herm_p(X, Y, rA ? k2_maskA<TA>(mk.x) : (mk.x & 63u), rA ? k2_maskA<TA>(mk.y) : (mk.y & 63u));
+            const bool rA = ph == 0 || ph == 3;  // round A: chunk bits 6..C-1, round B: bits 0..5
+            const uint32_t sh = rA ? (uint32_t)TA : 0u, keep = rA ? 63u & ~((1u << (6 - TA)) - 1u) : 63u;
+            butterfly_herm_p(X, Y, (mk.x >> sh) & keep, (mk.y >> sh) & keep);
             if (ph == 0) {
                 if constexpr (TA == 6) k2p_store_A(X, Y, wk, colA);
                 else k2p_store_A_g<TA>(X, Y, wk, t);
@@ -783,7 +784,8 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
             // conjugate transposes): round B, then round A
 #pragma unroll 1
             for (int ph = 0; ph < 2; ++ph) {
-                butterfly_herm_p(X, Y, ph ? k2_maskA<TA>(mk.x) : (mk.x & 63u), ph ? k2_maskA<TA>(mk.y) : (mk.y & 63u));
+                const uint32_t sh = ph ? (uint32_t)TA : 0u, keep = ph ? 63u & ~((1u << (6 - TA)) - 1u) : 63u;
+                butterfly_herm_p(X, Y, (mk.x >> sh) & keep, (mk.y >> sh) & keep);
                 if (ph == 0) {
                     k2p_store_B(X, Y, wk, t);
                     k2_bar_atom_g<TA>(half);
