@@ -7,6 +7,15 @@
 //   round A: chunk bits 6..11 in registers (element i = hi), thread t = lo
 //   round B: chunk bits 0..5  in registers (element j = lo), thread t = hi
 //
+// so the forward pass needs one shared-memory exchange per setting (A -> B)
+// and the adjoint two (A -> B after the forward round A, B -> A before the
+// inverse round A), half of what three 4-bit rounds need.  A CTA runs two
+// atoms, k0 = 2 kp (warps 0-1) and k0 + 1 (warps 2-3), on the same bin and
+// high pattern: they share the staged setting metadata (and, in the adjoint,
+// the dense c buffer), and the four warps reach all 128 TMEM lanes.  This file
+// holds the forward kernel on scalar complex registers; the adjoint kernel,
+// on packed FP32 pairs, is in qst_tworound_packed.cuh.
+//
 // Chunks of C = 10 or 11 qubits (whole states of 10, 11 qubits) keep 64
 // amplitudes per thread with 2^(C-6) threads per atom (TA = C - 6 thread
 // bits), so a CTA of 128 threads runs 2^(13-C) atoms:
@@ -17,14 +26,6 @@
 //
 // (chunk bits TA..5 sit in both rounds' registers; round B transforms them).
 // The exchange buffer keeps u at row u / 64, column u mod 64.
-// so the forward pass needs one shared-memory exchange per setting (A -> B)
-// and the adjoint two (A -> B after the forward round A, B -> A before the
-// inverse round A), half of what three 4-bit rounds need.  A CTA runs two
-// atoms, k0 = 2 kp (warps 0-1) and k0 + 1 (warps 2-3), on the same bin and
-// high pattern: they share the staged setting metadata (and, in the adjoint,
-// the dense c buffer), and the four warps reach all 128 TMEM lanes.  This file
-// holds the forward kernel on scalar complex registers; the adjoint kernel,
-// on packed FP32 pairs, is in qst_tworound_packed.cuh.
 //
 // Exchange buffer (one per atom): u at 66 hi + lo.  Round-A accesses (lanes
 // over lo) are contiguous; round-B accesses (lanes over hi, pairs of lo as
