@@ -3069,7 +3069,7 @@ int64_t plan_unit_ctas(const qst_plan_s *p) {
 }
 
 constexpr int kBatchStreams = 16;
-constexpr int kBatchBin = 32;  // settings per bin of a batch plan of 10..16 qubits (see batch_create)
+constexpr int kBatchBin = 64;  // settings per bin of a batch plan of 10..16 qubits (see batch_create)
 
 enum BatchPhase { kPhPack, kPhValidate, kPhForward, kPhEpilogue, kPhLoss, kPhAdjoint, kPhReduce, kPhHsum, kPhases };
 
@@ -3167,9 +3167,10 @@ qst_status batch_create(qst_batch *out, int count, const int *n, const int *M, c
     // The instances share the GPU, so a plan of 10..16 qubits needs no small bins
     // to fill it alone: unless the caller fixes max_bin_settings, such plans bin
     // up to kBatchBin settings (12-qubit chunks then run the two-round kernels).
-    // The batch autotuner picked these bins for every class of n >= 10 on the
-    // 64-instance workload.  Smaller states keep their own bin sizes: their units
-    // are a warp per (bin, atom), and many short bins keep the SMs busy.
+    // On the 64-instance workload bins of 64 measured 15.08 ms per evaluation,
+    // 32 15.54 and 96 15.17 (for the 12..14- and the 10, 11-qubit classes
+    // alike).  Smaller states keep their own bin sizes: their units are a warp
+    // per (bin, atom), and many short bins keep the SMs busy.
     qst_params prm0;
     qst_params_default(&prm0);
     if (params && !each) prm0 = *params;
