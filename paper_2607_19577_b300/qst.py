@@ -642,9 +642,10 @@ def batch_candidates(n):
         return ([dict(fixed_rounds=3, max_bin_settings=sm) for sm in (0, 8, 32)] +
                 [dict(fixed_rounds=0, max_bin_settings=sm) for sm in (0, 32)])
     if 10 <= n <= 11:
-        return [dict(fixed_rounds=0, max_bin_settings=sm, reg_bits=rb) for sm in (0, 32, 96) for rb in (4, 5)]
+        return ([dict(fixed_rounds=2, max_bin_settings=sm) for sm in (0, 32, 64, 96)] +
+                [dict(fixed_rounds=0, max_bin_settings=sm, reg_bits=rb) for sm in (0, 32, 96) for rb in (4, 5)])
     if 12 <= n <= 16:
-        return [dict(fixed_rounds=fr, max_bin_settings=sm) for fr in (2, 1) for sm in (0, 32, 96)]
+        return [dict(fixed_rounds=fr, max_bin_settings=sm) for fr in (2, 1) for sm in (0, 32, 64, 96)]
     return [dict()]
 
 
