@@ -640,13 +640,15 @@ __global__ void __launch_bounds__(k2T, 2) k_adjoint_2r_multi(const AdjArgs *__re
 // refills for setting si + 1 was last read by itself (setting si - 1).
 // How many entries per setting are staged (the scatter reads the rest from
 // global memory) trades latency against occupancy:
-//   * k_adjoint_2c stages 32: a CTA takes 74,000 B of shared memory and, with
-//     at most 168 registers a thread, three CTAs (12 warps) share an SM.  The
-//     n = 16, M = 4096, K = 16 launch (about 120 entries per setting and
-//     chunk) takes 5.63 ms, against 5.82 with 512 staged at two CTAs per SM;
+//   * k_adjoint_2c stages none in shared memory: each thread loads its first
+//     two entries of the next setting into registers at the end of the current
+//     one.  A CTA takes 71,952 B and, with at most 168 registers a thread,
+//     three CTAs (12 warps) share an SM.  The n = 16, M = 4096, K = 16 launch
+//     (about 120 entries per setting and chunk) takes 5.54 ms, against 5.63
+//     with 32 entries staged by cp.async and 5.82 with 512 at two CTAs per SM;
 //   * k_adjoint_2c_multi (the batch, whose settings hold up to 5000 entries
 //     per chunk) stages 512 at two CTAs per SM: 4.79 against 5.16 ms with 32.
-constexpr int k2cStageSingle = 32;  // observed entries per setting and atom staged by cp.async
+constexpr int k2cStageSingle = 0;   // observed entries per setting and atom staged by cp.async
 constexpr int k2cStageMulti = 512;
 struct K2cSmem {
     int work, stage_u, stage_c, stage_p, masks, meta, tmem, total;
@@ -747,7 +749,29 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
     // only its z write is skipped.  Larger atoms are whole warps.
     const bool run = TA >= 5 ? active : true;
     if (run) {
+        // k2cStage == 0: each thread loads its first two entries of the next
+        // setting into registers at the end of the current one (X, Y are dead
+        // there, so the loads cost no registers at the kernel's peak) and finds
+        // them in flight-completed registers at the next scatter.
+        uint32_t ru[2] = {0u, 0u};
+        float rc[2] = {0.f, 0.f};
+        float2 rp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        auto prefetch = [&](int si) {
+            if (si < bcount) {
+                const SetMeta mt = meta_sm[si];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = (int)t + (e << TA);
+                    if (j < mt.cnt) {
+                        ru[e] = outcome[mt.lo + j];
+                        rc[e] = c_obs[mt.lo + j];
+                        rp[e] = phk[mt.lo + j];
+                    }
+                }
+            }
+        };
         auto issue = [&](int si) {
+            if constexpr (k2cStage == 0) return;
             if (si < bcount) {
                 const SetMeta mt = meta_sm[si];
                 const int nst = mt.cnt < SA ? mt.cnt : SA;
@@ -760,13 +784,32 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
             }
             cp_async_commit();
         };
-        issue(0);
+        if constexpr (k2cStage == 0) prefetch(0);
+        else issue(0);
         for (int si = 0; si < bcount; ++si) {
             const uint2 mk = masks_sm[si];
             const SetMeta mt = meta_sm[si];
-            cp_async_wait0();  // this thread's entries of setting si have landed
-            issue(si + 1);     // into the buffer this thread read for setting si - 1
-            {
+            if constexpr (k2cStage == 0) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = (int)t + (e << TA);
+                    if (j < mt.cnt) {
+                        const uint32_t pos = k2p_pos(ru[e] & cmask);
+                        const float cy = rc[e] * mt.cs;
+                        wk[pos] = cy * rp[e].x;
+                        wk[k2pPlane + pos] = cy * rp[e].y;
+                    }
+                }
+                for (int j = (int)t + (2 << TA); j < mt.cnt; j += (1 << TA)) {
+                    const uint32_t pos = k2p_pos(outcome[mt.lo + j] & cmask);
+                    const float cy = c_obs[mt.lo + j] * mt.cs;
+                    const float2 ph = phk[mt.lo + j];
+                    wk[pos] = cy * ph.x;
+                    wk[k2pPlane + pos] = cy * ph.y;
+                }
+            } else {
+                cp_async_wait0();  // this thread's entries of setting si have landed
+                issue(si + 1);     // into the buffer this thread read for setting si - 1
                 const int o = (si & 1) * SA;
                 for (int j = t; j < mt.cnt; j += (1 << TA)) {
                     const bool st = j < SA;
@@ -803,6 +846,7 @@ __device__ __forceinline__ void adjoint_2c_body(const AdjArgs a, const int cta) 
                 }
             }
             k2p_tm_acc(t_z, X, Y);
+            if constexpr (k2cStage == 0) prefetch(si + 1);
             k2_bar_atom_g<TA>(half);  // every position is zero again before the next scatter
         }
         cp_async_wait0();
