@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-iterations", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance batched evaluation (field batched; single rank only)")
+    ap.add_argument("--no-wide", action="store_true",
+                    help="skip the n = 20, M = 1024, K = 8 evaluation (field n20; default workload, single rank)")
     ap.add_argument("--shard", action="store_true",
                     help="each rank evaluates a contiguous shard of the settings with the global B and the ranks "
                          "all-reduce (loss, grad, grad_w) every step (measurement partition of Sec. III-B); "
@@ -356,6 +358,45 @@ def batched_eval(flush, reps=10, autotune=False):
                             "table": [{"n": n, "params": c, "ms": ms} for n, c, ms in table],
                             "how": "qst.autotune_batch: per size class, the class's instances timed as one batch "
                                    "under each candidate layout; the fastest per class"}
+    return out
+
+
+def wide_eval(flush, reps=3):
+    """The n = 20, M = 1024, K = 8 workload (synth.make_instance("n20_m1024_k8",
+    seed=0), 10,000 shots a setting): qst_evaluate on the default plan (the wide
+    path) with the transform cache (phi_cache = 1) and recomputing the rotated
+    amplitudes in the adjoint (phi_cache = 0), CUDA events on the current
+    stream, L2 flushed before each timed evaluation, preallocated outputs."""
+    import torch
+    from paper_2607_19577_b300 import qst, synth
+    inst = synth.make_instance("n20_m1024_k8", seed=0)
+    n, M, K = inst.n, inst.M, inst.K
+    amps = M * K * (1 << n)
+    data = qst.Data.from_numpy(n, inst.basis, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+    psi, w = torch.from_numpy(inst.psi).cuda(), torch.from_numpy(inst.w).cuda()
+    outs = (torch.empty(inst.nnz, dtype=torch.float32, device="cuda"),
+            torch.empty(inst.nnz, dtype=torch.float32, device="cuda"),
+            torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty_like(psi), torch.empty_like(w))
+    out = {"workload": "n20_m1024_k8", "amplitudes_per_eval": int(amps), "unit": "amplitudes/s"}
+    for name, cache in (("cached", 1), ("recompute", 0)):
+        plan = qst.Plan(n, M, K, inst.nnz, eps=inst.eps, phi_cache=cache)
+        for _ in range(2):
+            plan.evaluate(psi, w, data, *outs)
+        total = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.evaluate(psi, w, data, *outs)
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        plan.check()
+        out[name] = {"ms_per_eval": total / reps, "value": amps / (total / reps) * 1e3,
+                     "geometry": plan.geometry()}
+        plan.close()
+    out["how"] = (f"qst_evaluate, {reps} timed evaluations after 2 untimed, L2 flushed before each; "
+                  "cached: the adjoint reads the forward's transforms at the observed outcomes")
     return out
 
 
@@ -715,6 +756,9 @@ def run_ours(args):
     batched = None
     if ws == 1 and not args.no_batched and not args.shard:
         batched = batched_eval(flush, autotune=args.autotune)
+    wide = None
+    if ws == 1 and not args.no_wide and not args.shard and args.workload == WORKLOAD:
+        wide = wide_eval(flush)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -750,7 +794,7 @@ def run_ours(args):
                            "parallelism": (f"setting shards over {ws} ranks + all-reduce of (loss, grad, grad_w)"
                                            if args.shard else ("replicas" if ws > 1 else "single GPU"))},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-                "algorithm1": algo, "batched": batched,
+                "algorithm1": algo, "batched": batched, "n20": wide,
                 "gpu_launches": launches, "kernels": kern, "wall_ms_per_step": 1e3 * t_wall / args.steps,
                 "workspace_bytes": plan.workspace_bytes()}
         print(json.dumps(line), flush=True)
