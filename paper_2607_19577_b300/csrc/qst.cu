@@ -1738,8 +1738,9 @@ qst_status qst_plan_create(qst_plan *out, int n, int M, int K, int64_t nnz, cons
     }
     // qst_evaluate's transform cache: K x nnz complex values (1 GB for the
     // n = 16, M = 4096, K = 16 workload); automatic for two-round plans up to 16 GiB
-    // (on the wide path with 12-qubit chunks, n = 20, only when asked for: there the adjoint
-    // recomputes by default)
+    // (for whole states of 10, 11 qubits only with sparse outcomes; on the wide path
+    // with 12-qubit chunks, n = 20, only when asked for: there the adjoint recomputes
+    // by default); always held by cluster plans, whose adjoint reads transforms
     if (!rc && nnz > 0 &&
         ((p->fx2 && (prm.phi_cache == 1 || (prm.phi_cache == -1 && (int64_t)K * nnz * 8 <= ((int64_t)16 << 30) &&
                                             (c == 12 || sparse)))) ||
