@@ -130,14 +130,18 @@ def _schedule(t, T_alpha, T_ref):
 
 @pytest.mark.parametrize("name,n,K,T,T_alpha,T_ref,rounds", [("n4_all81", None, 4, 14, 3, 7, -1),
                                                               ("n12_m60_k6", 12, 6, 9, 4, 0, -1),
-                                                              ("n12_m60_k5", 12, 5, 8, 3, 7, 2)])
+                                                              ("n12_m60_k5", 12, 5, 8, 3, 7, 2),
+                                                              ("n11_m40_k5", 11, 5, 8, 3, 7, 2),
+                                                              ("n17_m12_k3", 17, 3, 6, 3, 5, 4)])
 def test_device_iterations_equal_host_steps(name, n, K, T, T_alpha, T_ref, rounds):
     """qst_iterate (every decision on the device, one captured graph) equals the same
     schedule driven from the host with qst_step: bitwise the same atoms and weights
     and the same J after every iteration.  A second run continues (t0 = T) and a
     replay of the first run's graph on the same buffers reproduces it.  The last
     case runs the two-round chunk kernels (odd K: a CTA with one atom), whose
-    forward honours the device skip flag inside conditional graph nodes."""
+    forward honours the device skip flag inside conditional graph nodes.  The
+    11-qubit case runs the two-round kernels with four atoms per CTA, the 17-qubit
+    case the 16-qubit chunks on CTA clusters (fixed_rounds = 4)."""
     inst = synth.make_instance(name, seed=11, K=K)
     psi0 = inst.psi.astype(np.complex128)
     psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
