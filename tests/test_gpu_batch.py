@@ -183,3 +183,32 @@ def test_batch_iterate_equals_per_instance_iterate():
         assert torch.equal(p, first[idx][2]) and torch.equal(w, first[idx][3])
     assert sum(int(f[1].sum()) for f in first) > 0
     b.close()
+
+
+def test_batch_with_cluster_and_small_chunk_plans():
+    """A batch holding a 16-qubit-chunk plan (CTA clusters: the batch then runs
+    every instance's own launch sequence in the graph) beside two-round plans of
+    10, 11 qubits equals the same plans called directly, bitwise, and the oracle."""
+    insts = [synth.random_instance(17, 6, 2, 1500, 41), synth.random_instance(11, 30, 3, 400, 42),
+             synth.random_instance(10, 25, 5, 1500, 43)]
+    params = [dict(chunk_qubits=16), dict(), dict()]
+    b = qst.Batch([(i.n, i.M, i.K, i.nnz) for i in insts], params=params)
+    datas, psis, ws, losses, cs, gs, gws = _alloc(insts)
+    b.evaluate(psis, ws, datas, losses, cs, gs, gws)
+    torch.cuda.synchronize()
+    assert b.plan(0).geometry()["fixed_rounds"] == 4
+    assert b.plan(1).geometry()["fixed_rounds"] == 2 and b.plan(2).geometry()["fixed_rounds"] == 2
+    for idx, inst in enumerate(insts):
+        p1, c1, l1, g1, gw1 = b.plan(idx).evaluate(psis[idx], ws[idx], datas[idx])
+        torch.cuda.synchronize()
+        assert l1.item() == losses[idx].item()
+        assert torch.equal(c1, cs[idx]) and torch.equal(g1, gs[idx]) and torch.equal(gw1, gws[idx])
+        psi = inst.psi.astype(np.complex128)
+        w = inst.w.astype(np.float64)
+        f = oracle.forward(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, inst.count, inst.shots)
+        a = oracle.adjoint(inst.n, inst.basis, psi, w, inst.row_ptr, inst.outcome, f["c_obs"])
+        assert abs(losses[idx].item() - f["loss"]) <= 1e-5 * abs(f["loss"])
+        gg = gs[idx].cpu().numpy().astype(np.complex128)
+        for k in range(inst.K):
+            assert np.max(np.abs(gg[k] - a["grad_psi"][k])) <= 1e-4 * np.max(np.abs(a["grad_psi"][k]))
+    b.close()
